@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: preconditioned-OMM solves per second on one GB300 (replicas on N GPUs).
+
+One step = one whole solve of the 2D 128^2 smooth-field workload (n = 16384, N = 128
+states, 16 conformal poles, GMRES(15) x 5 at rtol 1e-5 with the sparsifying
+preconditioner, mixed precision): set the starting block, filter it with the pole
+expansion, run the preconditioned CG with the exact quartic line search, and evaluate
+the energy and residual in FP64.  Inputs are resident in HBM when the timed region
+starts; the GMRES working set (~8 GB) is far larger than L2.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a bounded
+sample of the same workload, extrapolated to solves/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OMM solves/sec and H-apply GB/s at E err≤1e-8 vs FP64 form; p50/p99 latency"
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="smooth2d-128")
+    ap.add_argument("--iters", type=int, default=0, help="fixed CG iterations (0: energy criterion)")
+    ap.add_argument("--no-fp64-check", action="store_true", help="skip the untimed FP64-form comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=1, help="per-kernel CUDA-event timing in the timed region")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------ workload
+def load_workload(name):
+    from workloads import WORKLOADS
+    wl = WORKLOADS[name]
+    spectra = json.load(open(os.path.join(ROOT, "workloads", "spectra.json")))[name]
+    return wl, spectra
+
+
+def workload_config(wl, spectra, iters, precision="mixed"):
+    return {"workload": f"{wl.name}: {wl.dim}D {wl.m}^{wl.dim} periodic grid (n={wl.n}), N={wl.N} states, "
+                        f"P={wl.P} conformal poles, {wl.potential} potential, {precision}",
+            "grid": [wl.m] * wl.dim, "box_len": wl.L, "N": wl.N, "P": wl.P, "precision": precision,
+            "inner_preconditioner": "sparsifying (nested-dissection multifrontal LU)",
+            "gmres": "restart 15, <=5 cycles, rtol 1e-5", "cg_iters": iters if iters else "energy criterion",
+            "l2": "inputs/working set larger than L2 (GMRES basis ~GBs)", "parallelism": "replicas",
+            "spectral_interval": "stored exact [lam_1, lam_N], lam_{N+1} (workloads/spectra.json)"}
+
+
+# ------------------------------------------------------------------------------ CPU oracle timing
+def oracle_sample(wl, spectra, budget_s=12.0):
+    """Time the FP64 oracle's pole solves (the dominant work) on a bounded sample and
+    extrapolate to solves/s: one solve = (1 filter + CG iterations) preconditioner
+    applications, each P x N GMRES solves."""
+    import numpy as np
+    from oracle import poles as opoles
+    from oracle.precond import PolePreconditioner
+    V = wl.potential_values()
+    z, w = opoles.poles_conformal(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
+    X0 = wl.initial_block()
+    cols = 2
+    pc = PolePreconditioner(wl.shape, wl.L, V, spectra["sigma"], z[:1], w[:1], mode="gmres", inner="spp")
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        pc(X0[reps % (wl.N // cols) * cols:(reps % (wl.N // cols) + 1) * cols])
+        reps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = (time.perf_counter() - t0) / reps
+    return t, cols
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return 1
+
+
+def cpu_baseline_record(wl, spectra, applications):
+    t, cols = oracle_sample(wl, spectra)
+    per_solve = t * (wl.P * wl.N / cols) * applications
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle GMRES+sparsifying pole solve, 1 pole x {cols} columns ({t:.2f} s), scaled by "
+                       f"P*N/{cols} systems x {applications} preconditioner applications per solve; pocketfft and "
+                       f"SuperLU single-threaded (BLAS pool {threads_used()} threads)")}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, spectra = load_workload(a.workload)
+    applications = 1 + (a.iters or 12)
+    t0 = time.perf_counter()
+    vals = []
+    for s in range(a.warmup + a.steps):
+        t, cols = oracle_sample(wl, spectra, budget_s=4.0)
+        if s >= a.warmup:
+            vals.append(1.0 / (t * (wl.P * wl.N / cols) * applications))
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    rec = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(wl, spectra, a.iters, "fp64 oracle"),
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                            "sample": f"each step: one oracle pole solve (1 pole x 2 columns, ~4 s), extrapolated "
+                                      f"to P*N systems x {applications} applications per solve; wall {wall:.1f} s"},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(rec))
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1603_09724_gb300 as omm
+
+    wl, spectra = load_workload(a.workload)
+    V = wl.potential_values()
+    mixed = wl.precision == "mixed"
+    prec = omm.OMM_MIXED if mixed else omm.OMM_FP64
+    cdt = torch.complex64 if mixed else torch.complex128
+    z, w = omm.poles_fermi(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
+    tol = 0.0 if a.iters else (1e-10 if mixed else 1e-13)
+    maxit = a.iters if a.iters else 40
+    prm = omm.default_params(precision=prec, maxit=maxit, tol=tol)
+    s = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
+    t_setup = time.perf_counter()
+    s.set_poles(z, w)
+    t_setup = time.perf_counter() - t_setup
+    X0h = torch.from_numpy(wl.initial_block(np.complex64 if mixed else np.complex128)).pin_memory()
+    X0 = X0h.to("cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.set_orbitals(X0)
+        return s.solve()
+
+    for _ in range(a.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if a.profile:
+        s.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat = []
+    for _ in range(a.steps):
+        ls = torch.cuda.Event(enable_timing=True)
+        le = torch.cuda.Event(enable_timing=True)
+        ls.record(stream)
+        st = step()
+        le.record(stream)
+        lat.append((ls, le))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile_read() if a.profile else None
+    if a.profile:
+        s.profile(False)
+    clk = clocks.stop()
+    lat_ms = sorted(x.elapsed_time(y) for x, y in lat)
+    tmax = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(tmax.item())
+    value = world * a.steps / (ms_max / 1000.0)
+
+    # end to end through the public API with host buffers (pinned), copies in the timed region
+    Xout = torch.empty_like(X0h).pin_memory()
+    Xdev = torch.empty_like(X0)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(a.steps):
+        Xdev.copy_(X0h, non_blocking=True)
+        s.set_orbitals(Xdev)
+        s.solve()
+        s.get_orbitals(Xdev)
+        Xout.copy_(Xdev, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    nbytes = X0h.numel() * X0h.element_size()
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    rec = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c64" if mixed else "c128", "data": "synthetic",
+           "config": workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64"),
+           "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
+           "solve": {"iters": st["iters"], "filters": st["filters"], "converged": st["converged"],
+                     "energy_fp64": st["energy_fp64"], "resid_fp64": st["resid_fp64"],
+                     "E_rel_err_vs_exact": abs(st["energy_fp64"] - spectra["E_ref"]) / abs(spectra["E_ref"]),
+                     "gmres_iters_max": st["gmres_iters_max"], "gmres_iters_total": st["gmres_iters_total"],
+                     "setup_s_all_poles": t_setup},
+           "clocks": clk,
+           "e2e": {"value": world * a.steps / (e2e_ms / 1000.0), "unit": "solves/s",
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}
+    if prof:
+        dom = max(prof, key=lambda k: prof[k]["ms"])
+        rec["gpu_launches"] = int(sum(v["kernels"] for v in prof.values()))
+        kern = {}
+        for k, v in prof.items():
+            if v["calls"]:
+                kern[k] = {"calls": v["calls"], "kernels": v["kernels"], "ms": round(v["ms"], 3),
+                           "share": round(v["ms"] / max(ms, 1e-9), 4),
+                           "GB_s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1) if v["bytes"] else None}
+        rec["kernels"] = kern
+        d = prof[dom]
+        ach = d["bytes"] / max(d["ms"], 1e-9) / 1e6
+        rec["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                           "frac": ach / hbm, "traffic": None,
+                           "note": "achieved = algorithmic bytes / CUDA-event time summed over the class's "
+                                   "launches in the timed region; peak = measured copy bandwidth"}
+        ha = prof["happly"]
+        rec["happly_GB_s"] = ha["bytes"] / max(ha["ms"], 1e-9) / 1e6
+    if not a.no_fp64_check and world == 1:
+        rec["accuracy_vs_fp64"] = fp64_compare(a, wl, spectra, s, omm, torch, V, z, w)
+    if not a.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline_record(wl, spectra, st["filters"] + st["iters"])
+    print(json.dumps(rec))
+
+
+def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w):
+    """The same solve in the plain FP64 form (untimed): energy and subspace agreement."""
+    import numpy as np
+    try:
+        Xm = s.get_orbitals().cpu().numpy().astype(np.complex128)
+        prm =omm.default_params(precision=omm.OMM_FP64, maxit=a.iters if a.iters else 40,
+                                 tol=0.0 if a.iters else 1e-13)
+        t0 = time.perf_counter()
+        s64 = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
+        s64.set_poles(z, w)
+        s64.set_orbitals(torch.from_numpy(wl.initial_block(np.complex128)).to("cuda"))
+        st = s64.solve()
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        X64 = s64.get_orbitals().cpu().numpy()
+        Q1, _ = np.linalg.qr(Xm.T)
+        Q2, _ = np.linalg.qr(X64.T)
+        sin = float(np.linalg.norm(Q1 - Q2 @ (Q2.conj().T @ Q1), 2))
+        Em = s.energy()
+        s64.close()
+        return {"E_rel_diff": abs(Em - st["energy_fp64"]) / abs(st["energy_fp64"]), "sin_angle": sin,
+                "fp64_form_iters": st["iters"], "fp64_form_E_rel_err_vs_exact":
+                    abs(st["energy_fp64"] - spectra["E_ref"]) / abs(spectra["E_ref"]),
+                "fp64_form_solve_s": t64}
+    except Exception as e:   # report, never hide
+        return {"error": repr(e)}
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

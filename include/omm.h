@@ -1,0 +1,217 @@
+/*
+ * omm.h -- C ABI of the GB300 library for the preconditioned orbital minimization method
+ * (Lu & Yang, "Preconditioning orbital minimization method for planewave
+ * discretization", arXiv:1603.09724).
+ *
+ * Problem (Sec. 1, eq. tracemin; Sec. 4 eq. ex1mat): H = -Delta/2 + V on the periodic box
+ * [0, L)^d, discretised pseudospectrally on an m^d grid (kinetic symbol (2 pi^2/L^2)|k|^2,
+ * k in [-m/2, m/2)^d), shifted by sigma so that H - sigma < 0.  The library minimises
+ * E_omm(X) = 1/2 tr((2I - X^*X) X^*(H - sigma)X) (eq. omm) over X in C^{n x N} by the
+ * preconditioned nonlinear CG of Algorithm 1 with an exact quartic line search; the
+ * preconditioner is the pole expansion of the Fermi projector (Sec. 3.1, eqs. dFOP,
+ * direct, lst): P R = sum_j w_j (H - sigma - z_j)^-1 R, each shifted system solved
+ * roughly by restarted GMRES whose right preconditioner is the sparsifying
+ * preconditioner of Sec. 3.2 (eqs. GLu, QG, P), set up once per pole on the host and
+ * applied on the device by triangular solves.
+ *
+ * Layout conventions
+ *   - A grid function is n = m^d contiguous complex values, x index fastest
+ *     (flat index x + m*(y + m*z)), real/imaginary interleaved.
+ *   - A block of N grid functions is column-major: column j at offset j*n.
+ *   - Complex type: complex128 (two doubles) when the handle precision is OMM_FP64,
+ *     complex64 (two floats) when it is OMM_MIXED.  V is always double on input.
+ *   - Pointers documented as "device" must be CUDA device (or managed) memory of the
+ *     current device; "host" pointers are ordinary host memory.
+ * Ownership: inputs are copied or only read during the call; the handle owns all of its
+ * device state and frees it in omm_destroy.  Device pointers passed in are borrowed
+ * for the duration of the call.
+ * Streams: every device operation is enqueued on the stream given to omm_create.  Calls
+ * that return host values (energies, statistics) synchronise that stream; the others are
+ * asynchronous with respect to the host.
+ * Threads: a handle must not be used by two threads at once.  No C++ exception crosses
+ * this interface; every call returns an omm_status.
+ */
+#ifndef OMM_H
+#define OMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct omm_ctx* omm_t;
+
+typedef enum {
+  OMM_OK = 0,
+  OMM_EINVAL = -1,        /* invalid argument (null pointer, bad size, bad interval)    */
+  OMM_ENOMEM = -2,        /* device or host allocation failed                            */
+  OMM_EUNSUPPORTED = -3,  /* grid size / dimension / option not supported                */
+  OMM_ENOTCONV = -4,      /* iteration limit reached (statistics are still filled)       */
+  OMM_ETIMEOUT = -5,      /* a bounded device-side wait gave up                          */
+  OMM_ECUDA = -6,         /* a CUDA runtime call failed (see omm_last_error_message)     */
+  OMM_ESHIFT = -7,        /* H - sigma is not negative definite (E_omm unbounded below)  */
+  OMM_ESTATE = -8         /* call out of order (e.g. iterate before poles are set)       */
+} omm_status;
+
+typedef enum { OMM_FP64 = 0, OMM_MIXED = 1 } omm_precision;
+
+/* Right preconditioner of the GMRES pole solves. */
+typedef enum {
+  OMM_INNER_SPARSIFY = 0,  /* sparsifying preconditioner P^-1 Q G (Sec. 3.2)               */
+  OMM_INNER_KINETIC = 1,   /* shifted kinetic inverse G = (T + <V> - sigma - z)^-1 (PP, Test 1) */
+  OMM_INNER_NONE = 2       /* no preconditioner                                              */
+} omm_inner;
+
+typedef struct {
+  int dim;         /* 2 or 3                                    */
+  int m[3];        /* points per dimension (equal; 2^a 3^b)     */
+  double box_len;  /* L: the box is [0, L)^dim                  */
+} omm_grid;
+
+typedef struct {
+  int precision;        /* omm_precision                                               */
+  int inner;            /* omm_inner                                                   */
+  int gmres_m;          /* restart length (Sec. 4: 15), 1..15                          */
+  int gmres_cycles;     /* maximum number of cycles (Sec. 4: 5)                        */
+  double gmres_rtol;    /* relative residual tolerance per system (Sec. 4: 1e-5)      */
+  int gmres_fixed;      /* 1: run every cycle to gmres_m steps (no tolerance test)     */
+  int stencil_radius;   /* radius r of the (2r+1)^d sparsifying stencil (1)            */
+  double pivot_floor;   /* static pivoting: pivots below pivot_floor*|row| are raised  */
+  double tol;           /* CG stop: |E_{m+1} - E_m| <= tol |E_{m+1}| (Sec. 4: 1e-13)   */
+  int maxit;            /* maximum CG iterations per round                             */
+  int refilter;         /* extra (filter + CG) rounds after the first                  */
+} omm_params;
+
+typedef struct {
+  int iters;               /* CG iterations done                                       */
+  int filters;             /* filter applications (1 + refilter rounds run)            */
+  int converged;           /* 1 if the energy criterion was met                        */
+  double energy;           /* E_omm after the last step, from the iteration's Grams    */
+  double energy_fp64;      /* E_omm recomputed in FP64 (omm_solve / omm_energy)        */
+  double resid_fp64;       /* ||HX - X S^-1 K||_F / ||HX||_F in FP64 (omm_solve)       */
+  double gmres_relres_max; /* largest GMRES residual estimate of the last pole solve   */
+  int gmres_iters_max;     /* largest GMRES step count of the last pole solve          */
+  int gmres_iters_total;   /* sum of GMRES steps over all CG iterations (max per call) */
+} omm_stats;
+
+/* Human-readable text for a status code (static storage). */
+const char* omm_strerror(omm_status s);
+/* Text of the last CUDA failure recorded by this thread (static per-thread storage). */
+const char* omm_last_error_message(void);
+
+/* Defaults: FP64, sparsifying inner preconditioner, GMRES(15) x 5 cycles, rtol 1e-5
+ * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter. */
+omm_status omm_default_params(omm_params* p);
+
+/* Diagonal shift (Sec. 1): sigma = T_max + max(max V, 0) + 1e-3 (T_max + max V - min V),
+ * T_max = (2 pi^2/L^2) sum_d (m/2)^2.  By Weyl's inequality H - sigma < 0.
+ * V: host, n doubles.  Errors: OMM_EINVAL. */
+omm_status omm_default_shift(const omm_grid* g, const double* V, double* shift);
+
+/* Create a handle.  V: host, n doubles, copied.  N: number of states (1 <= N < n).
+ * shift: sigma; must exceed T_max + max V (else OMM_ESHIFT).  p: NULL for defaults.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Allocates the device work
+ * space for the CG and for P_max = 32 poles' GMRES on the current device.
+ * Errors: OMM_EINVAL, OMM_EUNSUPPORTED (grid), OMM_ESHIFT, OMM_ENOMEM, OMM_ECUDA. */
+omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, const omm_params* p,
+                      void* stream, omm_t* out);
+void omm_destroy(omm_t h);
+
+/* Pole rules (host helpers, no handle).  z, w: host, 2P doubles each (re, im pairs).
+ *
+ * omm_poles_fermi: quadrature of the contour integral of eq. FOP by the conformal map of
+ * an annulus (Sec. 3.1, eq. dFOP): the strip 0 < Im u < K' is mapped by s = sn(u; k) and
+ * a Moebius map onto the plane minus [a, b] (occupied: lam_1 .. lam_N, a may be any lower
+ * bound) and [c, +inf) (unoccupied, c <= lam_{N+1}); P trapezoid nodes on Im u = K'/2.
+ * Error decays like exp(-pi K' P / (4K)).  Needs a < b < c and P >= 2 even.
+ * omm_poles_circle: trapezoid rule on |z - center| = radius (r(lam) = 1/(1+((lam-c)/R)^P)). */
+omm_status omm_poles_fermi(double a, double b, double c, int P, double* z, double* w);
+omm_status omm_poles_circle(double center, double radius, int P, double* z, double* w);
+
+/* Set the pole expansion P R = sum_j w_j (H - sigma - z_j)^-1 R (eq. dFOP): z, w host,
+ * 2P doubles each; 1 <= P <= 32.  With the sparsifying inner preconditioner this builds,
+ * for every pole, the stencil row q (SVD of G(a, a^c), eq. QG), the sparse matrix P_j
+ * (eq. P), its nested-dissection multifrontal LU (host, FP64) and uploads the factors.
+ * Errors: OMM_EINVAL, OMM_ENOMEM, OMM_ECUDA. */
+omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w);
+
+/* Copy the current orbitals in (X: device, n x N, handle precision) or out. */
+omm_status omm_set_orbitals(omm_t h, const void* X);
+omm_status omm_get_orbitals(omm_t h, void* X);
+
+/* Filter the orbitals once: X <- P X (Sec. 4: the starting guess is filtered).
+ * Errors: OMM_ESTATE if no poles are set. */
+omm_status omm_filter(omm_t h);
+
+/* k steps of Algorithm 1 from the current X (restarting the CG: the first step uses the
+ * steepest preconditioned direction).  st may be NULL.  Returns OMM_OK, or OMM_ESHIFT if
+ * the quartic was not bounded below. */
+omm_status omm_iterate(omm_t h, int k, omm_stats* st);
+
+/* Whole solve: filter, CG until the energy criterion or maxit, then refilter rounds,
+ * then the FP64 energy and residual of the result.  Returns OMM_ENOTCONV (with st
+ * filled) if maxit was reached in the last round. */
+omm_status omm_solve(omm_t h, omm_stats* st);
+
+/* E_omm of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams). */
+omm_status omm_energy(omm_t h, double* E);
+
+/* ---- building blocks on caller buffers (the steps of one iteration) ------------ */
+
+/* Y = (H - sigma - s) X for ncols columns: X, Y device, n x ncols, handle precision;
+ * s = s_re + i s_im (pass s = -sigma for the unshifted -Delta/2 + V). */
+omm_status omm_apply_h(omm_t h, const void* X, void* Y, int ncols, double s_re, double s_im);
+
+/* C = A^* B (na x nb, complex128, row-major, device, ldc = nb): A, B device blocks of
+ * na and nb columns in the handle precision. */
+omm_status omm_gram(omm_t h, const void* A, int na, const void* B, int nb, void* C);
+
+/* Grad = 2 HX - X (X^*HX) - HX (X^*X) with H = H - sigma (Sec. 2.1): X device block of
+ * N columns; HX and Grad device blocks (HX computed internally; may be NULL). */
+omm_status omm_gradient(omm_t h, const void* X, void* HX, void* Grad);
+
+/* Quartic coefficients c[5] of E_omm(X + tD) and the exact line-search step *t
+ * (host outputs); X, D device blocks of N columns. */
+omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double* t);
+
+/* Sparsifying preconditioner of pole j on ncols columns: U = P_j^-1 Q_j (G_j B)
+ * (Sec. 3.2).  B, U device, handle precision.  Errors: OMM_ESTATE without poles or if
+ * the inner preconditioner is not OMM_INNER_SPARSIFY. */
+omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncols);
+
+/* Pole-expansion preconditioner on N columns: Y = sum_j w_j Y_j with Y_j the GMRES
+ * solution of (H - sigma - z_j) Y_j = R started from R (Sec. 3.1 eqs. direct, lst).
+ * R, Y device blocks of N columns.  st may be NULL (fills the gmres_* fields). */
+omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
+
+/* Statistics of the sparsifying factor of pole j (host outputs, any may be NULL):
+ * number of supernodes, factor entries (L + U), smallest |pivot| / largest |pivot|,
+ * number of perturbed pivots. */
+omm_status omm_factor_info(omm_t h, int pole, int* nsuper, long long* nnz, double* pivot_ratio, int* nperturbed);
+
+/* Device allocator hook used by subsequent omm_create calls (NULL, NULL restores
+ * cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or NULL. */
+omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx);
+
+/* Bytes of device memory the handle holds. */
+omm_status omm_device_bytes(omm_t h, size_t* bytes);
+
+/* ---- instrumentation (no counterpart in the paper; used to report roofline figures) --
+ * Kernel classes: 0 happly (H-apply), 1 greenq (Green symbol + Q stencil), 2 trsv
+ * (sparsifying triangular solves, L and U), 3 orth (GMRES Gram-Schmidt), 4 gram,
+ * 5 block_update (gradient), 6 vector (axpby, dots, GMRES vector updates),
+ * 7 small (line search, Givens, counters).  For every class the handle always counts
+ * calls, kernels launched and algorithmic bytes moved; with profiling enabled it also
+ * brackets each call with CUDA events on the handle's stream and sums the elapsed
+ * milliseconds.  omm_profile_enable(h, 1) resets the counters; omm_profile_read
+ * synchronises the stream.  omm_profile_class_name returns NULL for an unknown class. */
+omm_status omm_profile_enable(omm_t h, int on);
+omm_status omm_profile_read(omm_t h, int cls, long long* calls, long long* kernels, double* ms, double* bytes);
+const char* omm_profile_class_name(int cls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMM_H */

@@ -1,0 +1,1142 @@
+// C ABI of the OMM library: handle, device memory, pole setup and the iteration driver.
+//
+// One preconditioned CG step (Algorithm 1) on the device, with H = H0 - sigma and the
+// unshifted H0 X kept (the shift enters only the FP64 N x N algebra):
+//   Grad = 2 H0X - X (K0 + 2 sigma (I - S)) - H0X S          (Sec. 2.1, rearranged)
+//   G = -sum_j w_j Y_j, (H - z_j) Y_j = Grad by batched GMRES  (Sec. 3.1 eqs. direct, lst)
+//   beta = Re<G, G - G_prev> / <G_prev, G_prev>, D = G + beta D (Polak-Ribiere)
+//   HD = H0 D; Grams [X D]^*[X D H0X H0D]; quartic c_0..c_4; exact line search t
+//   X += t D, H0X += t H0D; the Grams of the new X follow from the quartic expansion.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "spp.h"
+#include "trsv.h"
+
+using namespace omm;
+
+namespace {
+
+thread_local std::string g_last_error;
+void* (*g_alloc)(size_t, void*) = nullptr;
+void (*g_free)(void*, void*) = nullptr;
+void* g_alloc_ctx = nullptr;
+std::mutex g_alloc_mu;
+
+constexpr int PMAX = 32;
+constexpr int KMAXB = 16;
+
+}  // namespace
+
+void omm_internal_set_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  g_last_error = std::string(cudaGetErrorString(e)) + " in " + what + " (" + file + ":" + std::to_string(line) + ")";
+}
+
+enum ProfClass { PC_HAPPLY = 0, PC_GREENQ, PC_TRSV, PC_ORTH, PC_GRAM, PC_BLOCKUPD, PC_VEC, PC_SMALL, PC_NCLS };
+const char* const kProfNames[PC_NCLS] = {"happly", "greenq", "trsv", "orth", "gram", "block_update", "vector", "small"};
+
+struct Prof {
+  bool on = false;
+  double ms[PC_NCLS] = {};
+  long long calls[PC_NCLS] = {};
+  long long kernels[PC_NCLS] = {};
+  double bytes[PC_NCLS] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> pending;   // class, first event index
+};
+
+struct omm_ctx {
+  int dim = 2, m = 0;
+  size_t n = 0;
+  int N = 0;
+  double L = 1.0, shift = 0.0, kin = 0.0, lmean = 0.0;
+  omm_params prm{};
+  bool dbl = true;
+  size_t csz = 16;
+  cudaStream_t st = nullptr;
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*release)(void*, void*) = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  std::vector<double> Vh;
+
+  // device state
+  void* V = nullptr;       // n reals (working precision)
+  void* V64 = nullptr;     // n doubles (FP64 check)
+  void* tw = nullptr;      // m twiddles (working precision)
+  void* tw64 = nullptr;
+  void* blk = nullptr;     // [X | D | HX | HD], each N columns
+  void* Grad = nullptr;
+  void* G = nullptr;
+  void* Gp = nullptr;
+  double2* gram = nullptr;  // 2N x 4N
+  void* gram_work = nullptr;
+  void* M1 = nullptr;
+  void* M2 = nullptr;
+  OmmScalars* sc = nullptr;
+  OmmScalars* sc_h = nullptr;  // pinned
+  void* red_work = nullptr;
+  double2* shifts = nullptr;   // [PMAX] sigma + z_p
+  double2* zero_shift = nullptr;
+  double2* tmp_shift = nullptr;
+  double2* wts = nullptr;      // [PMAX] w_p
+  int* nact_d = nullptr;
+  int* nact_h = nullptr;       // pinned
+  // FP64 check work
+  void* X64 = nullptr;
+  void* HX64 = nullptr;
+  double2* gram64 = nullptr;
+  void* gram64_work = nullptr;
+  void* fft_tmp = nullptr;
+  size_t fft_tmp_bytes = 0;
+  void* gw_dbg = nullptr;       // Gram work for omm_gram / the residual check
+  size_t gw_dbg_bytes = 0;
+  double2* g2 = nullptr;        // (2N)^2 Gram for the residual check
+  int Pfac = 0;                 // poles the factor buffers are sized for
+
+  // poles
+  int P = 0;
+  std::vector<double2> z, w;
+  bool poles_set = false;
+  // GMRES work (sized for P poles)
+  int Palloc = 0;
+  void* Vb = nullptr;
+  void* Zb = nullptr;
+  void* xs = nullptr;
+  void* wv = nullptr;
+  void* tv = nullptr;
+  double2* Hh = nullptr;
+  double2* cs = nullptr;
+  double2* gv = nullptr;
+  double2* yv = nullptr;
+  double* beta = nullptr;
+  double* bnorm = nullptr;
+  int* active = nullptr;
+  int* steps = nullptr;
+  int* itot = nullptr;
+  double* est = nullptr;
+  // inner preconditioner data
+  void* ghat = nullptr;   // P * n (working precision)
+  void* qd = nullptr;     // P * nq
+  int nq = 1;
+  // sparsifying factor
+  SppStructure spp;
+  bool spp_built = false;
+  std::vector<SppPole> spp_poles;
+  void* factor = nullptr;
+  void* ynd = nullptr;
+  void* ubuf = nullptr;
+  int* d_node_ns = nullptr;
+  int* d_node_nb = nullptr;
+  int* d_node_off = nullptr;
+  int* d_node_boff = nullptr;
+  int* d_node_uoff = nullptr;
+  long long* d_node_fss = nullptr;
+  long long* d_node_fbs = nullptr;
+  long long* d_node_fsb = nullptr;
+  int* d_perm = nullptr;
+  int* d_bnat = nullptr;
+  int* d_cptr = nullptr;
+  int* d_cidx = nullptr;
+  int* d_levels = nullptr;
+  size_t trsv_smem = 0;
+  int last_gmres_max = 0;
+  double last_relres_max = 0.0;
+  int gmres_total = 0;
+
+  Prof prof;
+
+  void prof_flush() {
+    if (prof.pending.empty()) return;
+    cudaStreamSynchronize(st);
+    for (auto& pe : prof.pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, prof.pool[pe.second], prof.pool[pe.second + 1]) == cudaSuccess) prof.ms[pe.first] += t;
+    }
+    prof.pending.clear();
+    prof.used = 0;
+  }
+  size_t prof_event_pair() {
+    if (prof.used + 2 > prof.pool.size()) {
+      if (prof.pool.size() < 4096) {
+        while (prof.pool.size() < 4096) {
+          cudaEvent_t e;
+          if (cudaEventCreate(&e) != cudaSuccess) break;
+          prof.pool.push_back(e);
+        }
+      }
+      if (prof.used + 2 > prof.pool.size()) prof_flush();
+    }
+    const size_t i = prof.used;
+    prof.used += 2;
+    return i;
+  }
+
+  ~omm_ctx() {
+    prof.pending.clear();
+    for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
+    for (void* p : allocs) {
+      if (release) release(p, alloc_ctx);
+      else cudaFree(p);
+    }
+    if (sc_h) cudaFreeHost(sc_h);
+    if (nact_h) cudaFreeHost(nact_h);
+  }
+
+  omm_status dalloc(void** p, size_t b) {
+    *p = nullptr;
+    if (b == 0) b = 16;
+    b = (b + 255) / 256 * 256;
+    if (alloc) {
+      *p = alloc(b, alloc_ctx);
+      if (!*p) return OMM_ENOMEM;
+    } else {
+      cudaError_t e = cudaMalloc(p, b);
+      if (e != cudaSuccess) {
+        omm_internal_set_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+        *p = nullptr;
+        return OMM_ENOMEM;
+      }
+    }
+    allocs.push_back(*p);
+    bytes += b;
+    return OMM_OK;
+  }
+  template <typename P_>
+  omm_status dalloc_t(P_** p, size_t b) {
+    void* v = nullptr;
+    omm_status s = dalloc(&v, b);
+    *p = (P_*)v;
+    return s;
+  }
+  void* col(void* base, size_t j) const { return (char*)base + j * n * csz; }
+  void* X() const { return col(blk, 0); }
+  void* D() const { return col(blk, N); }
+  void* HX() const { return col(blk, 2 * N); }
+  void* HD() const { return col(blk, 3 * N); }
+};
+
+namespace {
+
+omm_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return OMM_OK;
+  omm_internal_set_cuda_error(e, what, __FILE__, __LINE__);
+  return OMM_ECUDA;
+}
+
+// Times one launch group on the handle's stream when profiling is on; always counts the
+// kernels launched and their algorithmic bytes.
+struct ProfScope {
+  omm_ctx* h;
+  int cls;
+  size_t ev = (size_t)-1;
+  ProfScope(omm_ctx* h_, int cls_, double bytes, int nk) : h(h_), cls(cls_) {
+    h->prof.calls[cls] += 1;
+    h->prof.kernels[cls] += nk;
+    h->prof.bytes[cls] += bytes;
+    if (h->prof.on) {
+      ev = h->prof_event_pair();
+      cudaEventRecord(h->prof.pool[ev], h->st);
+    }
+  }
+  ~ProfScope() {
+    if (ev != (size_t)-1) {
+      cudaEventRecord(h->prof.pool[ev + 1], h->st);
+      h->prof.pending.push_back({cls, ev});
+    }
+  }
+};
+#define PROF(cls, bytes, nk, expr)                 \
+  do {                                             \
+    ProfScope _ps(h, (cls), (double)(bytes), (nk)); \
+    OMM_TRY(expr);                                 \
+  } while (0)
+
+double kinetic_max(int dim, int m, double L) {
+  const double c = 2.0 * M_PI * M_PI / (L * L);
+  return c * dim * (double)(m / 2) * (m / 2);
+}
+
+bool radix_ok(int m) {
+  if (m < 2) return false;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+omm_status ensure_fft_tmp(omm_ctx* h, size_t ncols, bool dbl);
+
+// H0 X (shift 0) or (H0 - s_g) X for ncols columns; fused single-CTA kernel when the grid
+// fits shared memory, else the multi-pass kernels
+omm_status happly(omm_ctx* h, const void* X, void* Y, int ncols, const double2* shifts, int cpg, const int* active,
+                  bool fp64 = false) {
+  const bool dbl = fp64 || h->dbl;
+  const void* V = fp64 ? h->V64 : h->V;
+  const void* tw = fp64 ? h->tw64 : h->tw;
+  const double kn = h->kin / (double)h->n;
+  const double bytes = (2.0 * ncols * (dbl ? 16 : 8) + (dbl ? 8 : 4)) * (double)h->n;
+  if (fused_fft_supported(h->dim, h->m, dbl)) {
+    PROF(PC_HAPPLY, bytes, 1,
+         cuda_status(launch_happly(dbl, h->dim, h->m, X, Y, ncols, V, shifts, cpg, tw, kn, active, h->st), "happly"));
+    return OMM_OK;
+  }
+  OMM_TRY(ensure_fft_tmp(h, ncols, dbl));
+  PROF(PC_HAPPLY, bytes, h->dim == 3 ? 5 : 3,
+       cuda_status(launch_happly_big(dbl, h->dim, h->m, X, Y, ncols, V, shifts, cpg, tw, kn, active, h->fft_tmp, h->st),
+                   "happly"));
+  return OMM_OK;
+}
+
+omm_status greenq(omm_ctx* h, const void* B, void* Out, int ncols, int nq, int cpg, const int* active,
+                  const void* ghat = nullptr, const void* q = nullptr) {
+  if (!ghat) ghat = h->ghat;
+  if (!q) q = h->qd;
+  const double bytes = (2.0 * ncols + (double)((ncols + cpg - 1) / cpg)) * h->csz * (double)h->n;
+  if (fused_fft_supported(h->dim, h->m, h->dbl)) {
+    PROF(PC_GREENQ, bytes, 1,
+         cuda_status(launch_greenq(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, h->st),
+                     "greenq"));
+    return OMM_OK;
+  }
+  OMM_TRY(ensure_fft_tmp(h, ncols, h->dbl));
+  PROF(PC_GREENQ, bytes, h->dim == 3 ? 6 : 4,
+       cuda_status(
+           launch_greenq_big(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, h->fft_tmp, h->st),
+           "greenq"));
+  return OMM_OK;
+}
+
+omm_status ensure_dbg_work(omm_ctx* h, size_t need) {
+  if (h->gw_dbg_bytes >= need) return OMM_OK;
+  OMM_TRY(h->dalloc(&h->gw_dbg, need));
+  h->gw_dbg_bytes = need;
+  return OMM_OK;
+}
+
+omm_status ensure_fft_tmp(omm_ctx* h, size_t ncols, bool dbl) {
+  const size_t need = ncols * h->n * (dbl ? 16 : 8);
+  if (h->fft_tmp_bytes >= need) return OMM_OK;
+  OMM_TRY(h->dalloc(&h->fft_tmp, need));   // the old buffer stays owned until destroy
+  h->fft_tmp_bytes = need;
+  return OMM_OK;
+}
+
+omm_status upload_twiddles(omm_ctx* h, void* dst, bool dbl) {
+  std::vector<double> t(2 * h->m);
+  for (int k = 0; k < h->m; ++k) {
+    t[2 * k] = std::cos(2.0 * M_PI * k / h->m);
+    t[2 * k + 1] = -std::sin(2.0 * M_PI * k / h->m);
+  }
+  if (dbl) return cuda_status(cudaMemcpyAsync(dst, t.data(), t.size() * 8, cudaMemcpyHostToDevice, h->st), "tw");
+  std::vector<float> f(t.begin(), t.end());
+  omm_status s = cuda_status(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->st), "tw");
+  if (s == OMM_OK) s = cuda_status(cudaStreamSynchronize(h->st), "tw sync");
+  return s;
+}
+
+omm_status upload_complex(omm_ctx* h, void* dst, const std::vector<cd>& v, bool dbl) {
+  if (dbl)
+    return cuda_status(cudaMemcpyAsync(dst, v.data(), v.size() * 16, cudaMemcpyHostToDevice, h->st), "upload");
+  std::vector<float> f(2 * v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    f[2 * i] = (float)v[i].real();
+    f[2 * i + 1] = (float)v[i].imag();
+  }
+  omm_status s = cuda_status(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->st), "upload");
+  if (s == OMM_OK) s = cuda_status(cudaStreamSynchronize(h->st), "upload sync");
+  return s;
+}
+
+template <typename T_>
+omm_status upload_vec(omm_ctx* h, T_** dst, const std::vector<T_>& v) {
+  OMM_TRY(h->dalloc_t(dst, v.size() * sizeof(T_)));
+  if (v.empty()) return OMM_OK;
+  return cuda_status(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T_), cudaMemcpyHostToDevice, h->st), "upload");
+}
+
+omm_status ensure_gmres_work(omm_ctx* h, int P) {
+  if (h->Palloc >= P) return OMM_OK;
+  const size_t S = (size_t)P * h->N;
+  const size_t vb = S * h->n * h->csz;
+  const int m = h->prm.gmres_m;
+  OMM_TRY(h->dalloc(&h->Vb, vb * (m + 1)));
+  OMM_TRY(h->dalloc(&h->Zb, vb * m));
+  OMM_TRY(h->dalloc(&h->xs, vb));
+  OMM_TRY(h->dalloc(&h->wv, vb));
+  OMM_TRY(h->dalloc(&h->tv, vb));
+  OMM_TRY(h->dalloc_t(&h->Hh, S * (KMAXB + 1) * KMAXB * sizeof(double2)));
+  OMM_TRY(h->dalloc_t(&h->cs, S * KMAXB * 2 * sizeof(double2)));
+  OMM_TRY(h->dalloc_t(&h->gv, S * (KMAXB + 1) * sizeof(double2)));
+  OMM_TRY(h->dalloc_t(&h->yv, S * KMAXB * sizeof(double2)));
+  OMM_TRY(h->dalloc_t(&h->beta, S * sizeof(double)));
+  OMM_TRY(h->dalloc_t(&h->bnorm, S * sizeof(double)));
+  OMM_TRY(h->dalloc_t(&h->active, S * sizeof(int)));
+  OMM_TRY(h->dalloc_t(&h->steps, S * sizeof(int)));
+  OMM_TRY(h->dalloc_t(&h->itot, S * sizeof(int)));
+  OMM_TRY(h->dalloc_t(&h->est, S * sizeof(double)));
+  h->Palloc = P;
+  return OMM_OK;
+}
+
+TrsvArgs trsv_args(omm_ctx* h, int Ncols, size_t S) {
+  TrsvArgs a;
+  a.node_ns = h->d_node_ns;
+  a.node_nb = h->d_node_nb;
+  a.node_off = h->d_node_off;
+  a.node_boff = h->d_node_boff;
+  a.node_uoff = h->d_node_uoff;
+  a.node_fss = h->d_node_fss;
+  a.node_fbs = h->d_node_fbs;
+  a.node_fsb = h->d_node_fsb;
+  a.perm = h->d_perm;
+  a.bnat = h->d_bnat;
+  a.contrib_ptr = h->d_cptr;
+  a.contrib_idx = h->d_cidx;
+  a.factor_size = h->spp.factor_size;
+  a.n = h->n;
+  a.N = Ncols;
+  a.S = S;
+  return a;
+}
+
+TrsvLevels trsv_levels(omm_ctx* h) {
+  TrsvLevels lv;
+  lv.nlevels = (int)h->spp.levels.size();
+  lv.nodes = h->d_levels;
+  int s = 0;
+  for (auto& l : h->spp.levels) {
+    lv.start.push_back(s);
+    lv.count.push_back((int)l.size());
+    s += (int)l.size();
+  }
+  return lv;
+}
+
+// Right preconditioner for S = P*N systems: Z = M^-1 V (natural order in and out)
+omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, const int* active, void* tmp) {
+  const int inner = h->prm.inner;
+  const size_t S = (size_t)P * Ncols;
+  if (inner == OMM_INNER_NONE) {
+    return cuda_status(cudaMemcpyAsync(Z, Vk, S * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "copy");
+  }
+  if (inner == OMM_INNER_KINETIC) return greenq(h, Vk, Z, (int)S, 1, Ncols, active);
+  OMM_TRY(greenq(h, Vk, tmp, (int)S, h->nq, Ncols, active));
+  TrsvArgs a = trsv_args(h, Ncols, S);
+  TrsvLevels lv = trsv_levels(h);
+  const double bytes = ((double)P * h->spp.factor_size + (4.0 * h->n + 2.0 * h->spp.urows) * (double)S) * h->csz;
+  PROF(PC_TRSV, bytes, 2 * lv.nlevels,
+       cuda_status(launch_spp_solve(h->dbl, a, lv, P, tmp, h->ynd, h->ubuf, Z, h->factor, active, h->trsv_smem, h->st),
+                   "spp"));
+  return OMM_OK;
+}
+
+omm_status read_nactive(omm_ctx* h, int* out) {
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->nact_h, h->nact_d, sizeof(int), cudaMemcpyDeviceToHost, h->st), "nact"));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "nact sync"));
+  *out = *h->nact_h;
+  return OMM_OK;
+}
+
+// out = sign * sum_p w_p Y_p, (H - sigma - z_p) Y_p = R by GMRES from Y_p = R
+omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
+  const int P = h->P, N = h->N;
+  KrylovDims d;
+  d.S = P * N;
+  d.N = N;
+  d.n = h->n;
+  d.m = h->prm.gmres_m;
+  const size_t vs = (size_t)d.S * h->n * h->csz;
+  auto Vk = [&](int k) { return (void*)((char*)h->Vb + (size_t)k * vs); };
+  auto Zk = [&](int k) { return (void*)((char*)h->Zb + (size_t)k * vs); };
+  const double rtol = h->prm.gmres_rtol;
+  const int fixed = h->prm.gmres_fixed;
+  OMM_TRY(cuda_status(cudaMemsetAsync(h->itot, 0, sizeof(int) * d.S, h->st), "memset"));
+  for (int cyc = 0; cyc < h->prm.gmres_cycles; ++cyc) {
+    OMM_TRY(cuda_status(cudaMemsetAsync(h->steps, 0, sizeof(int) * d.S, h->st), "memset"));
+    if (cyc == 0) {
+      OMM_TRY(happly(h, R, h->wv, N, h->zero_shift, N, nullptr));
+      PROF(PC_VEC, 3.0 * d.S * h->n * h->csz, 1,
+           cuda_status(launch_krylov_init0(h->dbl, d, R, h->wv, h->shifts, Vk(0), h->xs, h->beta, h->gv, h->bnorm,
+                                           h->active, rtol, fixed, h->st),
+                       "init0"));
+    } else {
+      OMM_TRY(happly(h, h->xs, h->wv, d.S, h->shifts, N, nullptr));
+      PROF(PC_VEC, 3.0 * d.S * h->n * h->csz, 1,
+           cuda_status(launch_krylov_restart(h->dbl, d, R, h->wv, Vk(0), h->beta, h->gv, h->bnorm, h->active, rtol,
+                                             fixed, h->st),
+                       "restart"));
+    }
+    if (!fixed) {
+      // count active systems after the cycle start
+      PROF(PC_SMALL, 0, 1, cuda_status(launch_count_active(d, h->active, h->nact_d, h->st), "count"));
+      int na = 0;
+      OMM_TRY(read_nactive(h, &na));
+      if (na == 0) break;
+    }
+    for (int k = 0; k < d.m; ++k) {
+      OMM_TRY(inner_apply(h, P, N, Vk(k), Zk(k), h->active, h->tv));
+      OMM_TRY(happly(h, Zk(k), h->wv, d.S, h->shifts, N, h->active));
+      PROF(PC_ORTH, (2.0 * (k + 1) + 3.0) * d.S * h->n * h->csz, 1,
+           cuda_status(launch_krylov_orth(h->dbl, d, k, h->Vb, h->wv, h->Hh, h->active, h->st), "orth"));
+      OMM_TRY(cuda_status(cudaMemsetAsync(h->nact_d, 0, sizeof(int), h->st), "memset"));
+      PROF(PC_SMALL, 0, 1,
+           cuda_status(launch_krylov_givens(d, k, h->Hh, h->cs, h->gv, h->bnorm, h->active, h->steps, h->est, rtol,
+                                            fixed, h->nact_d, h->st),
+                       "givens"));
+      if (!fixed && k + 1 < d.m) {
+        int na = 0;
+        OMM_TRY(read_nactive(h, &na));
+        if (na == 0) break;
+      }
+    }
+    PROF(PC_VEC, (d.m + 2.0) * d.S * h->n * h->csz, 2,
+         cuda_status(launch_krylov_update(h->dbl, d, h->Hh, h->gv, h->steps, h->yv, h->Zb, h->xs, h->itot, h->st),
+                     "update"));
+  }
+  PROF(PC_VEC, (double)(d.S + N) * h->n * h->csz, 1,
+       cuda_status(launch_pole_combine(h->dbl, d, P, h->wts, sign, h->xs, out, h->st), "combine"));
+  return OMM_OK;
+}
+
+omm_status gmres_stats(omm_ctx* h) {
+  const int S = h->P * h->N;
+  std::vector<int> it(S);
+  std::vector<double> e(S);
+  OMM_TRY(cuda_status(cudaMemcpyAsync(it.data(), h->itot, S * sizeof(int), cudaMemcpyDeviceToHost, h->st), "stats"));
+  OMM_TRY(cuda_status(cudaMemcpyAsync(e.data(), h->est, S * sizeof(double), cudaMemcpyDeviceToHost, h->st), "stats"));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "stats sync"));
+  h->last_gmres_max = *std::max_element(it.begin(), it.end());
+  h->last_relres_max = *std::max_element(e.begin(), e.end());
+  return OMM_OK;
+}
+
+omm_status read_scalars(omm_ctx* h) {
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->sc_h, h->sc, sizeof(OmmScalars), cudaMemcpyDeviceToHost, h->st), "sc"));
+  return cuda_status(cudaStreamSynchronize(h->st), "sc sync");
+}
+
+// Grams of the current X and the gradient update matrices (t = 0)
+omm_status start_cg(omm_ctx* h) {
+  OMM_TRY(happly(h, h->X(), h->HX(), h->N, h->zero_shift, h->N, nullptr));
+  PROF(PC_GRAM, 5.0 * h->N * h->n * h->csz, 2,
+       cuda_status(launch_gram(h->dbl, h->X(), h->N, h->blk, 4 * h->N, h->n, h->gram, 4 * h->N, h->gram_work, h->st),
+                   "gram"));
+  PROF(PC_SMALL, 0, 1,
+       cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 0, h->prm.tol, h->sc, h->M1, h->M2, h->st),
+                   "ls0"));
+  return OMM_OK;
+}
+
+omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* conv) {
+  OMM_TRY(start_cg(h));
+  const size_t cnt = (size_t)h->N * h->n;
+  *conv = false;
+  int it = 0;
+  for (; it < k; ++it) {
+    PROF(PC_BLOCKUPD, 3.0 * cnt * h->csz, 1,
+         cuda_status(launch_block_update(h->dbl, h->X(), h->HX(), h->M1, h->M2, 0.0, 2.0, h->N, h->n, h->Grad, h->st),
+                     "grad"));
+    OMM_TRY(pole_solve(h, h->Grad, h->G, -1.0));
+    PROF(PC_VEC, 2.0 * cnt * h->csz, 2,
+         cuda_status(launch_redot(h->dbl, cnt, h->G, h->G, &h->sc->gg, h->red_work, h->st), "dot"));
+    if (it > 0)
+      PROF(PC_VEC, 2.0 * cnt * h->csz, 2,
+           cuda_status(launch_redot(h->dbl, cnt, h->G, h->Gp, &h->sc->gdot, h->red_work, h->st), "dot"));
+    PROF(PC_SMALL, 0, 1, cuda_status(launch_pr_beta(h->sc, it == 0 ? 1 : 0, h->st), "beta"));
+    // D = G + beta D   (first step: D = G)
+    if (it == 0)
+      OMM_TRY(cuda_status(cudaMemcpyAsync(h->D(), h->G, cnt * h->csz, cudaMemcpyDeviceToDevice, h->st), "copy"));
+    else
+      PROF(PC_VEC, 3.0 * cnt * h->csz, 1,
+           cuda_status(launch_axpby(h->dbl, cnt, nullptr, h->G, &h->sc->beta_c, h->D(), h->st), "dir"));
+    OMM_TRY(happly(h, h->D(), h->HD(), h->N, h->zero_shift, h->N, nullptr));
+    PROF(PC_GRAM, 6.0 * cnt * h->csz, 2,
+         cuda_status(launch_gram(h->dbl, h->blk, 2 * h->N, h->blk, 4 * h->N, h->n, h->gram, 4 * h->N, h->gram_work,
+                                 h->st),
+                     "gram"));
+    PROF(PC_SMALL, 0, 1,
+         cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->st),
+                     "ls"));
+    // X += t D ; HX += t HD
+    PROF(PC_VEC, 3.0 * cnt * h->csz, 1,
+         cuda_status(launch_axpby(h->dbl, cnt, &h->sc->t_c, h->D(), &h->sc->one_c, h->X(), h->st), "upd"));
+    PROF(PC_VEC, 3.0 * cnt * h->csz, 1,
+         cuda_status(launch_axpby(h->dbl, cnt, &h->sc->t_c, h->HD(), &h->sc->one_c, h->HX(), h->st), "upd"));
+    std::swap(h->G, h->Gp);
+    OMM_TRY(read_scalars(h));
+    OMM_TRY(gmres_stats(h));
+    h->gmres_total += h->last_gmres_max;
+    if (h->sc_h->bad) {
+      *done_iters = it + 1;
+      return OMM_ESHIFT;
+    }
+    if (h->sc_h->converged) {
+      *conv = true;
+      ++it;
+      break;
+    }
+  }
+  *done_iters = it;
+  if (st) {
+    st->energy = h->sc_h->E1;
+    st->gmres_iters_max = h->last_gmres_max;
+    st->gmres_relres_max = h->last_relres_max;
+    st->gmres_iters_total = h->gmres_total;
+  }
+  return OMM_OK;
+}
+
+
+// FP64 energy E_omm and relative residual ||HX - X S^-1 K|| / ||HX|| of the current X:
+// X converted to complex double, FP64 H-apply (shift sigma) and FP64 Grams.
+omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
+  const int N = h->N;
+  const size_t cnt = (size_t)N * h->n;
+  if (!h->X64) {
+    OMM_TRY(h->dalloc(&h->X64, cnt * 16 * 2));   // [X | HX] in FP64
+    OMM_TRY(h->dalloc_t(&h->gram64, (size_t)N * 2 * N * sizeof(double2)));
+    OMM_TRY(h->dalloc(&h->gram64_work, gram_work_bytes(N, 2 * N, h->n)));
+    OMM_TRY(h->dalloc_t(&h->tmp_shift, sizeof(double2) * 2));
+  }
+  void* X64 = h->X64;
+  void* HX64 = (char*)h->X64 + cnt * 16;
+  if (h->dbl)
+    OMM_TRY(cuda_status(cudaMemcpyAsync(X64, h->X(), cnt * 16, cudaMemcpyDeviceToDevice, h->st), "copy"));
+  else
+    PROF(PC_VEC, 24.0 * cnt, 1, cuda_status(launch_convert(true, cnt, h->X(), X64, h->st), "convert"));
+  const double2 sh = make_double2(h->shift, 0.0);
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->tmp_shift, &sh, sizeof(sh), cudaMemcpyHostToDevice, h->st), "shift"));
+  OMM_TRY(happly(h, X64, HX64, N, h->tmp_shift, N, nullptr, true));
+  PROF(PC_GRAM, 3.0 * cnt * 16, 2,
+       cuda_status(launch_gram(true, X64, N, X64, 2 * N, h->n, h->gram64, 2 * N, h->gram64_work, h->st), "gram64"));
+  std::vector<double2> C((size_t)N * 2 * N);
+  OMM_TRY(cuda_status(cudaMemcpyAsync(C.data(), h->gram64, C.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->st),
+                      "gram64 d2h"));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
+  // E = 1/2 tr((2I - S) K) = tr K - 1/2 tr(S K)
+  double trK = 0.0, trSK = 0.0;
+  for (int i = 0; i < N; ++i) {
+    trK += C[(size_t)i * 2 * N + N + i].x;
+    for (int j = 0; j < N; ++j) {
+      const double2 s = C[(size_t)i * 2 * N + j], k = C[(size_t)j * 2 * N + N + i];
+      trSK += s.x * k.x - s.y * k.y;
+    }
+  }
+  *E = trK - 0.5 * trSK;
+  if (resid) {
+    // ||HX - X S^-1 K||_F^2 = tr(HX^*HX) - tr(K^* S^-1 K) needs HX^*HX; use the residual
+    // of the Rayleigh quotient through the Gram of [X HX] with itself.
+    std::vector<double2> C2((size_t)2 * N * 2 * N);
+    OMM_TRY(ensure_dbg_work(h, gram_work_bytes(2 * N, 2 * N, h->n)));
+    if (!h->g2) OMM_TRY(h->dalloc_t(&h->g2, C2.size() * sizeof(double2)));
+    PROF(PC_GRAM, 4.0 * cnt * 16, 2,
+         cuda_status(launch_gram(true, X64, 2 * N, X64, 2 * N, h->n, h->g2, 2 * N, h->gw_dbg, h->st), "gram64b"));
+    OMM_TRY(cuda_status(cudaMemcpyAsync(C2.data(), h->g2, C2.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->st),
+                        "d2h"));
+    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
+    // S (N x N), K = X^*HX, W = HX^*HX; r^2 = tr W - tr(K^* S^-1 K)
+    std::vector<cd> S((size_t)N * N), K((size_t)N * N);
+    double trW = 0.0;
+    for (int i = 0; i < N; ++i) {
+      trW += C2[(size_t)(N + i) * 2 * N + N + i].x;
+      for (int j = 0; j < N; ++j) {
+        const double2 s = C2[(size_t)i * 2 * N + j], k = C2[(size_t)i * 2 * N + N + j];
+        S[(size_t)i * N + j] = cd(s.x, s.y);
+        K[(size_t)i * N + j] = cd(k.x, k.y);
+      }
+    }
+    // solve S Y = K by Gaussian elimination with partial pivoting (N x N, host)
+    std::vector<cd> A(S), Y(K);
+    for (int c = 0; c < N; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < N; ++r)
+        if (std::abs(A[(size_t)r * N + c]) > std::abs(A[(size_t)piv * N + c])) piv = r;
+      if (piv != c)
+        for (int j = 0; j < N; ++j) {
+          std::swap(A[(size_t)c * N + j], A[(size_t)piv * N + j]);
+          std::swap(Y[(size_t)c * N + j], Y[(size_t)piv * N + j]);
+        }
+      const cd d = A[(size_t)c * N + c];
+      for (int r = c + 1; r < N; ++r) {
+        const cd f = A[(size_t)r * N + c] / d;
+        if (f == cd(0.0, 0.0)) continue;
+        for (int j = c; j < N; ++j) A[(size_t)r * N + j] -= f * A[(size_t)c * N + j];
+        for (int j = 0; j < N; ++j) Y[(size_t)r * N + j] -= f * Y[(size_t)c * N + j];
+      }
+    }
+    for (int c = N - 1; c >= 0; --c)
+      for (int j = 0; j < N; ++j) {
+        cd s = Y[(size_t)c * N + j];
+        for (int k = c + 1; k < N; ++k) s -= A[(size_t)c * N + k] * Y[(size_t)k * N + j];
+        Y[(size_t)c * N + j] = s / A[(size_t)c * N + c];
+      }
+    double trKY = 0.0;   // tr(K^* Y) = sum_ij conj(K_ij) Y_ij
+    for (size_t e = 0; e < (size_t)N * N; ++e) trKY += (std::conj(K[e]) * Y[e]).real();
+    const double r2 = std::max(0.0, trW - trKY);
+    *resid = std::sqrt(r2 / std::max(trW, 1e-300));
+  }
+  return OMM_OK;
+}
+
+omm_status build_spp(omm_ctx* h) {
+  if (!h->spp_built) {
+    h->spp = spp_build_structure(h->dim, h->m, h->prm.stencil_radius);
+    const SppStructure& s = h->spp;
+    h->trsv_smem = trsv_smem_bytes(h->dbl, s.max_ns, s.max_nb);
+    if (h->trsv_smem > 220 * 1024) return OMM_EUNSUPPORTED;
+    std::vector<int> ns, nb, off, boff, uoff, lev;
+    std::vector<long long> fss, fbs, fsb;
+    for (auto& nd : s.nodes) {
+      ns.push_back(nd.ns); nb.push_back(nd.nb); off.push_back(nd.off); boff.push_back(nd.boff);
+      uoff.push_back(nd.uoff); fss.push_back(nd.fss); fbs.push_back(nd.fbs); fsb.push_back(nd.fsb);
+    }
+    for (auto& l : s.levels) lev.insert(lev.end(), l.begin(), l.end());
+    OMM_TRY(upload_vec(h, &h->d_node_ns, ns));
+    OMM_TRY(upload_vec(h, &h->d_node_nb, nb));
+    OMM_TRY(upload_vec(h, &h->d_node_off, off));
+    OMM_TRY(upload_vec(h, &h->d_node_boff, boff));
+    OMM_TRY(upload_vec(h, &h->d_node_uoff, uoff));
+    OMM_TRY(upload_vec(h, &h->d_node_fss, fss));
+    OMM_TRY(upload_vec(h, &h->d_node_fbs, fbs));
+    OMM_TRY(upload_vec(h, &h->d_node_fsb, fsb));
+    OMM_TRY(upload_vec(h, &h->d_perm, s.perm));
+    OMM_TRY(upload_vec(h, &h->d_bnat, s.bnat));
+    OMM_TRY(upload_vec(h, &h->d_cptr, s.contrib_ptr));
+    OMM_TRY(upload_vec(h, &h->d_cidx, s.contrib_idx));
+    OMM_TRY(upload_vec(h, &h->d_levels, lev));
+    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
+    h->spp_built = true;
+  }
+  return OMM_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* omm_strerror(omm_status s) {
+  switch (s) {
+    case OMM_OK: return "success";
+    case OMM_EINVAL: return "invalid argument";
+    case OMM_ENOMEM: return "out of memory";
+    case OMM_EUNSUPPORTED: return "unsupported grid or option";
+    case OMM_ENOTCONV: return "iteration limit reached";
+    case OMM_ETIMEOUT: return "device wait timed out";
+    case OMM_ECUDA: return "CUDA error";
+    case OMM_ESHIFT: return "H - sigma is not negative definite";
+    case OMM_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* omm_last_error_message(void) { return g_last_error.c_str(); }
+
+omm_status omm_default_params(omm_params* p) {
+  if (!p) return OMM_EINVAL;
+  p->precision = OMM_FP64;
+  p->inner = OMM_INNER_SPARSIFY;
+  p->gmres_m = 15;
+  p->gmres_cycles = 5;
+  p->gmres_rtol = 1e-5;
+  p->gmres_fixed = 0;
+  p->stencil_radius = 1;
+  p->pivot_floor = 1e-12;
+  p->tol = 1e-13;
+  p->maxit = 50;
+  p->refilter = 0;
+  return OMM_OK;
+}
+
+omm_status omm_default_shift(const omm_grid* g, const double* V, double* shift) {
+  if (!g || !V || !shift || (g->dim != 2 && g->dim != 3) || g->m[0] < 2 || !(g->box_len > 0)) return OMM_EINVAL;
+  const int m = g->m[0];
+  const size_t n = (g->dim == 3) ? (size_t)m * m * m : (size_t)m * m;
+  double vmax = V[0], vmin = V[0];
+  for (size_t i = 1; i < n; ++i) {
+    vmax = std::max(vmax, V[i]);
+    vmin = std::min(vmin, V[i]);
+  }
+  const double tmax = kinetic_max(g->dim, m, g->box_len);
+  *shift = tmax + std::max(vmax, 0.0) + 1e-3 * (tmax + vmax - vmin);
+  return OMM_OK;
+}
+
+omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return OMM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = release;
+  g_alloc_ctx = ctx;
+  return OMM_OK;
+}
+
+omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, const omm_params* p, void* stream,
+                      omm_t* out) {
+  if (!g || !V || !out) return OMM_EINVAL;
+  *out = nullptr;
+  if (g->dim != 2 && g->dim != 3) return OMM_EINVAL;
+  const int m = g->m[0];
+  if (g->m[1] != m || (g->dim == 3 && g->m[2] != m) || !radix_ok(m) || !(g->box_len > 0)) return OMM_EUNSUPPORTED;
+  const size_t n = (g->dim == 3) ? (size_t)m * m * m : (size_t)m * m;
+  if (N < 1 || (size_t)N >= n) return OMM_EINVAL;
+  omm_params prm;
+  omm_default_params(&prm);
+  if (p) prm = *p;
+  if (prm.gmres_m < 1 || prm.gmres_m > 15 || prm.gmres_cycles < 1 || prm.maxit < 0 || prm.refilter < 0 ||
+      (prm.precision != OMM_FP64 && prm.precision != OMM_MIXED) || prm.inner < 0 || prm.inner > 2 ||
+      prm.stencil_radius != 1)
+    return OMM_EINVAL;
+  const bool dbl = prm.precision == OMM_FP64;
+  if (!fused_fft_supported(g->dim, m, dbl) && !big_fft_supported(g->dim, m)) return OMM_EUNSUPPORTED;
+  if (!fused_fft_supported(g->dim, m, true) && !big_fft_supported(g->dim, m)) return OMM_EUNSUPPORTED;
+  double vmax = V[0];
+  for (size_t i = 1; i < n; ++i) vmax = std::max(vmax, V[i]);
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(V[i])) return OMM_EINVAL;
+  if (!(shift > kinetic_max(g->dim, m, g->box_len) + vmax)) return OMM_ESHIFT;
+
+  omm_ctx* h = new (std::nothrow) omm_ctx();
+  if (!h) return OMM_ENOMEM;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->alloc = g_alloc;
+    h->release = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+  }
+  h->dim = g->dim;
+  h->m = m;
+  h->n = n;
+  h->N = N;
+  h->L = g->box_len;
+  h->shift = shift;
+  h->kin = 2.0 * M_PI * M_PI / (g->box_len * g->box_len);
+  h->prm = prm;
+  h->dbl = dbl;
+  h->csz = dbl ? 16 : 8;
+  h->st = (cudaStream_t)stream;
+  h->Vh.assign(V, V + n);
+  double lm = 0.0;
+  for (size_t i = 0; i < n; ++i) lm += V[i];
+  h->lmean = lm / n;
+  auto fail = [&](omm_status s) { delete h; return s; };
+  omm_status s;
+  const size_t cnt = (size_t)N * n;
+  if ((s = h->dalloc(&h->V, n * (dbl ? 8 : 4))) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->V64, n * 8)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->tw, m * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->tw64, m * 16)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->blk, 4 * cnt * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->Grad, cnt * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->G, cnt * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->Gp, cnt * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc_t(&h->gram, (size_t)2 * N * 4 * N * sizeof(double2))) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->gram_work, std::max(gram_work_bytes(2 * N, 4 * N, n), gram_work_bytes(N, 4 * N, n)))) !=
+      OMM_OK)
+    return fail(s);
+  if ((s = h->dalloc(&h->M1, (size_t)N * N * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->M2, (size_t)N * N * h->csz)) != OMM_OK) return fail(s);
+  if ((s = h->dalloc_t(&h->sc, sizeof(OmmScalars))) != OMM_OK) return fail(s);
+  if ((s = h->dalloc(&h->red_work, redot_work_bytes())) != OMM_OK) return fail(s);
+  if ((s = h->dalloc_t(&h->shifts, PMAX * sizeof(double2))) != OMM_OK) return fail(s);
+  if ((s = h->dalloc_t(&h->zero_shift, sizeof(double2))) != OMM_OK) return fail(s);
+  if ((s = h->dalloc_t(&h->wts, PMAX * sizeof(double2))) != OMM_OK) return fail(s);
+  if ((s = h->dalloc_t(&h->nact_d, sizeof(int))) != OMM_OK) return fail(s);
+  if (cudaMallocHost((void**)&h->sc_h, sizeof(OmmScalars)) != cudaSuccess) return fail(OMM_ENOMEM);
+  if (cudaMallocHost((void**)&h->nact_h, sizeof(int)) != cudaSuccess) return fail(OMM_ENOMEM);
+  if (dbl)
+    s = cuda_status(cudaMemcpyAsync(h->V, V, n * 8, cudaMemcpyHostToDevice, h->st), "V");
+  else {
+    std::vector<float> vf(V, V + n);
+    s = cuda_status(cudaMemcpyAsync(h->V, vf.data(), n * 4, cudaMemcpyHostToDevice, h->st), "V");
+    if (s == OMM_OK) s = cuda_status(cudaStreamSynchronize(h->st), "sync");
+  }
+  if (s != OMM_OK) return fail(s);
+  if ((s = cuda_status(cudaMemcpyAsync(h->V64, V, n * 8, cudaMemcpyHostToDevice, h->st), "V64")) != OMM_OK) return fail(s);
+  if ((s = upload_twiddles(h, h->tw, dbl)) != OMM_OK) return fail(s);
+  if ((s = upload_twiddles(h, h->tw64, true)) != OMM_OK) return fail(s);
+  if ((s = cuda_status(cudaMemsetAsync(h->zero_shift, 0, sizeof(double2), h->st), "memset")) != OMM_OK) return fail(s);
+  if ((s = cuda_status(cudaMemsetAsync(h->blk, 0, 4 * cnt * h->csz, h->st), "memset")) != OMM_OK) return fail(s);
+  if ((s = cuda_status(cudaMemsetAsync(h->sc, 0, sizeof(OmmScalars), h->st), "memset")) != OMM_OK) return fail(s);
+  if ((s = cuda_status(cudaStreamSynchronize(h->st), "sync")) != OMM_OK) return fail(s);
+  *out = h;
+  return OMM_OK;
+}
+
+void omm_destroy(omm_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
+  if (!h || !z || !w || P < 1 || P > PMAX) return OMM_EINVAL;
+  h->P = P;
+  h->z.resize(P);
+  h->w.resize(P);
+  std::vector<double2> sh(P);
+  for (int j = 0; j < P; ++j) {
+    h->z[j] = make_double2(z[2 * j], z[2 * j + 1]);
+    h->w[j] = make_double2(w[2 * j], w[2 * j + 1]);
+    sh[j] = make_double2(h->shift + z[2 * j], z[2 * j + 1]);
+  }
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->shifts, sh.data(), P * sizeof(double2), cudaMemcpyHostToDevice, h->st), "shifts"));
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->wts, h->w.data(), P * sizeof(double2), cudaMemcpyHostToDevice, h->st), "w"));
+  OMM_TRY(ensure_gmres_work(h, P));
+  const int inner = h->prm.inner;
+  if (inner == OMM_INNER_KINETIC || inner == OMM_INNER_SPARSIFY) {
+    const size_t n = h->n;
+    std::vector<cd> ghat_all(P * n);
+    std::vector<cd> q_all;
+    if (inner == OMM_INNER_SPARSIFY) {
+      OMM_TRY(build_spp(h));
+      h->spp_poles.assign(P, SppPole());
+      std::vector<std::vector<cd>> gh(P);
+      const int nth = std::max(1, std::min<int>(P, (int)std::thread::hardware_concurrency()));
+      std::vector<std::thread> th;
+      for (int t = 0; t < nth; ++t)
+        th.emplace_back([&, t]() {
+          for (int j = t; j < P; j += nth)
+            spp_setup_pole(h->spp, h->kin, h->Vh.data(), h->shift, cd(z[2 * j], z[2 * j + 1]), h->prm.pivot_floor,
+                           h->spp_poles[j], gh[j]);
+        });
+      for (auto& t : th) t.join();
+      h->nq = (int)h->spp.offsets.size() / 3;
+      q_all.resize((size_t)P * h->nq);
+      for (int j = 0; j < P; ++j) {
+        std::copy(gh[j].begin(), gh[j].end(), ghat_all.begin() + (size_t)j * n);
+        std::copy(h->spp_poles[j].q.begin(), h->spp_poles[j].q.end(), q_all.begin() + (size_t)j * h->nq);
+      }
+      const long long fs = h->spp.factor_size;
+      if (h->Pfac < P) {
+        OMM_TRY(h->dalloc(&h->factor, (size_t)P * fs * h->csz));
+        OMM_TRY(h->dalloc(&h->ubuf, (size_t)h->spp.urows * P * h->N * h->csz));
+        OMM_TRY(h->dalloc(&h->ynd, (size_t)P * h->N * n * h->csz));
+        h->Pfac = P;
+      }
+      std::vector<cd> fall((size_t)P * fs);
+      for (int j = 0; j < P; ++j) std::copy(h->spp_poles[j].factor.begin(), h->spp_poles[j].factor.end(), fall.begin() + (size_t)j * fs);
+      OMM_TRY(upload_complex(h, h->factor, fall, h->dbl));
+    } else {
+      std::vector<cd> gh;
+      for (int j = 0; j < P; ++j) {
+        green_symbol(h->dim, h->m, h->kin, h->lmean, h->shift, cd(z[2 * j], z[2 * j + 1]), gh);
+        std::copy(gh.begin(), gh.end(), ghat_all.begin() + (size_t)j * n);
+      }
+      h->nq = 1;
+      q_all.assign(P, cd(1.0, 0.0));
+    }
+    if (!h->ghat) {
+      OMM_TRY(h->dalloc(&h->ghat, (size_t)PMAX * n * h->csz));
+      OMM_TRY(h->dalloc(&h->qd, (size_t)PMAX * 27 * h->csz));
+    }
+    OMM_TRY(upload_complex(h, h->ghat, ghat_all, h->dbl));
+    OMM_TRY(upload_complex(h, h->qd, q_all, h->dbl));
+  }
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
+  h->poles_set = true;
+  return OMM_OK;
+}
+
+omm_status omm_set_orbitals(omm_t h, const void* X) {
+  if (!h || !X) return OMM_EINVAL;
+  return cuda_status(cudaMemcpyAsync(h->X(), X, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "set X");
+}
+
+omm_status omm_get_orbitals(omm_t h, void* X) {
+  if (!h || !X) return OMM_EINVAL;
+  return cuda_status(cudaMemcpyAsync(X, h->X(), (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "get X");
+}
+
+omm_status omm_filter(omm_t h) {
+  if (!h) return OMM_EINVAL;
+  if (!h->poles_set) return OMM_ESTATE;
+  OMM_TRY(pole_solve(h, h->X(), h->G, +1.0));
+  return cuda_status(cudaMemcpyAsync(h->X(), h->G, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "copy");
+}
+
+omm_status omm_iterate(omm_t h, int k, omm_stats* st) {
+  if (!h || k < 0) return OMM_EINVAL;
+  if (!h->poles_set) return OMM_ESTATE;
+  if (st) std::memset(st, 0, sizeof(*st));
+  h->gmres_total = 0;
+  int done = 0;
+  bool conv = false;
+  omm_status s = cg_steps(h, k, st, &done, &conv);
+  if (st) {
+    st->iters = done;
+    st->converged = conv;
+  }
+  return s;
+}
+
+omm_status omm_solve(omm_t h, omm_stats* st) {
+  if (!h) return OMM_EINVAL;
+  if (!h->poles_set) return OMM_ESTATE;
+  omm_stats loc;
+  std::memset(&loc, 0, sizeof(loc));
+  h->gmres_total = 0;
+  int total = 0;
+  bool conv = false;
+  for (int round = 0; round <= h->prm.refilter; ++round) {
+    OMM_TRY(omm_filter(h));
+    loc.filters++;
+    int done = 0;
+    OMM_TRY(cg_steps(h, h->prm.maxit, &loc, &done, &conv));
+    total += done;
+  }
+  loc.iters = total;
+  loc.converged = conv;
+  double E = 0.0, r = 0.0;
+  omm_status s = energy_fp64(h, &E, &r);
+  if (s == OMM_OK) {
+    loc.energy_fp64 = E;
+    loc.resid_fp64 = r;
+  } else if (s != OMM_EUNSUPPORTED) {
+    return s;
+  }
+  if (st) *st = loc;
+  return conv ? OMM_OK : OMM_ENOTCONV;
+}
+
+omm_status omm_energy(omm_t h, double* E) {
+  if (!h || !E) return OMM_EINVAL;
+  return energy_fp64(h, E, nullptr);
+}
+
+omm_status omm_apply_h(omm_t h, const void* X, void* Y, int ncols, double s_re, double s_im) {
+  if (!h || !X || !Y || ncols < 0) return OMM_EINVAL;
+  if (!h->tmp_shift) OMM_TRY(h->dalloc_t(&h->tmp_shift, sizeof(double2) * 2));
+  const double2 sh = make_double2(h->shift + s_re, s_im);
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->tmp_shift, &sh, sizeof(sh), cudaMemcpyHostToDevice, h->st), "shift"));
+  OMM_TRY(happly(h, X, Y, ncols, h->tmp_shift, ncols > 0 ? ncols : 1, nullptr));
+  return cuda_status(cudaStreamSynchronize(h->st), "sync");
+}
+
+omm_status omm_gram(omm_t h, const void* A, int na, const void* B, int nb, void* C) {
+  if (!h || !A || !B || !C || na < 1 || nb < 1) return OMM_EINVAL;
+  OMM_TRY(ensure_dbg_work(h, gram_work_bytes(na, nb, h->n)));
+  OMM_TRY(cuda_status(launch_gram(h->dbl, A, na, B, nb, h->n, (double2*)C, nb, h->gw_dbg, h->st), "gram"));
+  return cuda_status(cudaStreamSynchronize(h->st), "sync");
+}
+
+omm_status omm_gradient(omm_t h, const void* X, void* HX, void* Grad) {
+  if (!h || !X || !Grad) return OMM_EINVAL;
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->X(), X, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "X"));
+  OMM_TRY(start_cg(h));
+  OMM_TRY(cuda_status(
+      launch_block_update(h->dbl, h->X(), h->HX(), h->M1, h->M2, 0.0, 2.0, h->N, h->n, Grad, h->st), "grad"));
+  if (HX) {
+    // (H - sigma) X = H0 X - sigma X
+    OMM_TRY(cuda_status(cudaMemcpyAsync(HX, h->HX(), (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "c"));
+    if (!h->tmp_shift) OMM_TRY(h->dalloc_t(&h->tmp_shift, sizeof(double2) * 2));
+    const double2 ms[2] = {make_double2(-h->shift, 0.0), make_double2(1.0, 0.0)};
+    OMM_TRY(cuda_status(cudaMemcpyAsync(h->tmp_shift, ms, sizeof(ms), cudaMemcpyHostToDevice, h->st), "s"));
+    OMM_TRY(cuda_status(launch_axpby(h->dbl, (size_t)h->N * h->n, h->tmp_shift, h->X(), h->tmp_shift + 1, HX, h->st), "ax"));
+  }
+  return cuda_status(cudaStreamSynchronize(h->st), "sync");
+}
+
+omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double* t) {
+  if (!h || !X || !D) return OMM_EINVAL;
+  const size_t cnt = (size_t)h->N * h->n;
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->X(), X, cnt * h->csz, cudaMemcpyDeviceToDevice, h->st), "X"));
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->D(), D, cnt * h->csz, cudaMemcpyDeviceToDevice, h->st), "D"));
+  OMM_TRY(happly(h, h->X(), h->HX(), h->N, h->zero_shift, h->N, nullptr));
+  OMM_TRY(happly(h, h->D(), h->HD(), h->N, h->zero_shift, h->N, nullptr));
+  OMM_TRY(cuda_status(
+      launch_gram(h->dbl, h->blk, 2 * h->N, h->blk, 4 * h->N, h->n, h->gram, 4 * h->N, h->gram_work, h->st), "gram"));
+  OMM_TRY(cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->st),
+                      "ls"));
+  OMM_TRY(read_scalars(h));
+  if (c)
+    for (int i = 0; i < 5; ++i) c[i] = h->sc_h->c[i];
+  if (t) *t = h->sc_h->t;
+  return h->sc_h->bad ? OMM_ESHIFT : OMM_OK;
+}
+
+omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncols) {
+  if (!h || !B || !U || ncols < 1 || ncols > h->N) return OMM_EINVAL;
+  if (!h->poles_set || h->prm.inner != OMM_INNER_SPARSIFY) return OMM_ESTATE;
+  if (pole < 0 || pole >= h->P) return OMM_EINVAL;
+  // one pole, ncols systems: Green + stencil into the GMRES scratch, then the solves
+  const size_t n = h->n;
+  OMM_TRY(greenq(h, B, h->tv, ncols, h->nq, ncols, nullptr, (char*)h->ghat + (size_t)pole * n * h->csz,
+                 (char*)h->qd + (size_t)pole * h->nq * h->csz));
+  TrsvArgs a = trsv_args(h, ncols, (size_t)ncols);
+  TrsvLevels lv = trsv_levels(h);
+  const void* f = (char*)h->factor + (size_t)pole * h->spp.factor_size * h->csz;
+  OMM_TRY(cuda_status(launch_spp_solve(h->dbl, a, lv, 1, h->tv, h->ynd, h->ubuf, U, f, nullptr, h->trsv_smem, h->st),
+                      "spp"));
+  return cuda_status(cudaStreamSynchronize(h->st), "sync");
+}
+
+omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st) {
+  if (!h || !R || !Y) return OMM_EINVAL;
+  if (!h->poles_set) return OMM_ESTATE;
+  OMM_TRY(pole_solve(h, R, Y, 1.0));
+  OMM_TRY(gmres_stats(h));
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->gmres_iters_max = h->last_gmres_max;
+    st->gmres_relres_max = h->last_relres_max;
+  }
+  return OMM_OK;
+}
+
+omm_status omm_factor_info(omm_t h, int pole, int* nsuper, long long* nnz, double* pivot_ratio, int* nperturbed) {
+  if (!h) return OMM_EINVAL;
+  if (!h->poles_set || h->prm.inner != OMM_INNER_SPARSIFY) return OMM_ESTATE;
+  if (pole < 0 || pole >= h->P) return OMM_EINVAL;
+  const SppPole& pp = h->spp_poles[pole];
+  if (nsuper) *nsuper = (int)h->spp.nodes.size();
+  if (nnz) *nnz = h->spp.factor_size;
+  if (pivot_ratio) *pivot_ratio = pp.pivot_max > 0 ? pp.pivot_min / pp.pivot_max : 0.0;
+  if (nperturbed) *nperturbed = pp.nperturbed;
+  return OMM_OK;
+}
+
+omm_status omm_profile_enable(omm_t h, int on) {
+  if (!h) return OMM_EINVAL;
+  h->prof_flush();
+  if (on) {
+    for (int c = 0; c < PC_NCLS; ++c) {
+      h->prof.ms[c] = 0.0;
+      h->prof.calls[c] = 0;
+      h->prof.kernels[c] = 0;
+      h->prof.bytes[c] = 0.0;
+    }
+  }
+  h->prof.on = on != 0;
+  return OMM_OK;
+}
+
+omm_status omm_profile_read(omm_t h, int cls, long long* calls, long long* kernels, double* ms, double* bytes) {
+  if (!h || cls < 0 || cls >= PC_NCLS) return OMM_EINVAL;
+  h->prof_flush();
+  if (calls) *calls = h->prof.calls[cls];
+  if (kernels) *kernels = h->prof.kernels[cls];
+  if (ms) *ms = h->prof.ms[cls];
+  if (bytes) *bytes = h->prof.bytes[cls];
+  return OMM_OK;
+}
+
+const char* omm_profile_class_name(int cls) { return (cls >= 0 && cls < PC_NCLS) ? kProfNames[cls] : nullptr; }
+
+omm_status omm_device_bytes(omm_t h, size_t* bytes) {
+  if (!h || !bytes) return OMM_EINVAL;
+  *bytes = h->bytes;
+  return OMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Shared device/host helpers for the OMM library (complex arithmetic, error plumbing).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "omm.h"
+
+namespace omm {
+
+// Complex type of a working precision: float2 for the mixed form, double2 for FP64.
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+  C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk<C>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C a, S s) {
+  return mk<C>(a.x * s, a.y * s);
+}
+// a + b * c (complex fused)
+template <typename C> __host__ __device__ __forceinline__ C cfma(C b, C c, C a) {
+  return mk<C>(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
+}
+// a + conj(b) * c
+template <typename C> __host__ __device__ __forceinline__ C cfmac(C b, C c, C a) {
+  return mk<C>(fma(b.x, c.x, fma(b.y, c.y, a.x)), fma(b.x, c.y, fma(-b.y, c.x, a.y)));
+}
+// multiply by i * sgn (sgn = +1 or -1)
+template <int SGN, typename C> __host__ __device__ __forceinline__ C cmuli(C a) {
+  return SGN > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+
+template <typename Cd, typename Cs> __host__ __device__ __forceinline__ Cd ccast(Cs a) {
+  Cd r; r.x = (decltype(r.x))a.x; r.y = (decltype(r.y))a.y; return r;
+}
+
+}  // namespace omm
+
+#define OMM_CUDA_TRY(expr)                                              \
+  do {                                                                  \
+    cudaError_t _e = (expr);                                            \
+    if (_e != cudaSuccess) {                                            \
+      omm_internal_set_cuda_error(_e, #expr, __FILE__, __LINE__);       \
+      return OMM_ECUDA;                                                 \
+    }                                                                   \
+  } while (0)
+
+#define OMM_TRY(expr)                      \
+  do {                                     \
+    omm_status _s = (expr);                \
+    if (_s != OMM_OK) return _s;           \
+  } while (0)
+
+extern "C++" void omm_internal_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);

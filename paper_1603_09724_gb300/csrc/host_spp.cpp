@@ -1,0 +1,453 @@
+// Sparsifying preconditioner setup on the host in FP64 (Sec. 3.2).
+//
+//   G = (T + l - sigma - z)^-1 with l = <V> (eq. GLu), a circulant: G(i, j) = g[i - j]
+//   Q(j, a(j)) = q for every j: q = conj(u_min), u_min the left singular vector of
+//     G(a, a^c) for its smallest singular value (one-sided Jacobi SVD of G(a, a^c)^*) (eq. QG)
+//   P_{j, j+o} = q_o + (qG)_o (V_{j+o} - l) on the stencil, 0 elsewhere (eq. P)
+//   P = L U by nested dissection (recursive bisection of the periodic grid by grid
+//   lines / planes) and a multifrontal factorisation with dense fronts, no pivoting
+//   (pivots below pivot_floor * row size are raised and counted).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <set>
+
+#include "spp.h"
+
+namespace omm {
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+inline int wrap(int a, int m) { a %= m; return a < 0 ? a + m : a; }
+
+struct Box {
+  int lo[3], ext[3];
+  bool per[3];
+};
+
+struct Builder {
+  int dim, m, r;
+  SppStructure* st;
+  std::vector<std::vector<int>> node_pts;   // natural indices per node
+  std::vector<Box> node_box;
+  std::vector<int> node_children_a, node_children_b;
+
+  int flat(int x, int y, int z) const { return x + m * (y + m * z); }
+
+  void points(const Box& b, std::vector<int>& out) const {
+    const int ez = dim == 3 ? b.ext[2] : 1;
+    for (int tz = 0; tz < ez; ++tz)
+      for (int ty = 0; ty < b.ext[1]; ++ty)
+        for (int tx = 0; tx < b.ext[0]; ++tx)
+          out.push_back(flat(wrap(b.lo[0] + tx, m), wrap(b.lo[1] + ty, m), dim == 3 ? wrap(b.lo[2] + tz, m) : 0));
+  }
+
+  int add_node(std::vector<int>&& pts, const Box& b, int ca, int cb) {
+    node_pts.push_back(std::move(pts));
+    node_box.push_back(b);
+    node_children_a.push_back(ca);
+    node_children_b.push_back(cb);
+    return (int)node_pts.size() - 1;
+  }
+
+  int nd(const Box& b) {
+    bool anyper = false;
+    int maxext = 0;
+    for (int d = 0; d < dim; ++d) {
+      if (b.per[d]) anyper = true;
+      maxext = std::max(maxext, b.ext[d]);
+    }
+    for (int d = 0; d < dim; ++d)
+      if (b.ext[d] <= 0) return -1;
+    const int leaf_ext = (dim == 3) ? 4 : 8;
+    if (!anyper && maxext <= leaf_ext) {
+      std::vector<int> pts;
+      points(b, pts);
+      return add_node(std::move(pts), b, -1, -1);
+    }
+    // cut dimension: a periodic one first (largest), else the largest extent >= 3
+    int cd = -1;
+    for (int d = 0; d < dim; ++d)
+      if (b.per[d] && (cd < 0 || b.ext[d] > b.ext[cd])) cd = d;
+    if (cd < 0)
+      for (int d = 0; d < dim; ++d)
+        if (b.ext[d] >= 3 && (cd < 0 || b.ext[d] > b.ext[cd])) cd = d;
+    if (cd < 0) {
+      std::vector<int> pts;
+      points(b, pts);
+      return add_node(std::move(pts), b, -1, -1);
+    }
+    Box c1 = b, c2 = b, s1 = b, s2 = b;
+    std::vector<int> sep;
+    if (b.per[cd]) {
+      const int h = m / 2;
+      c1.per[cd] = c2.per[cd] = false;
+      c1.lo[cd] = 1; c1.ext[cd] = h - 1;
+      c2.lo[cd] = h + 1; c2.ext[cd] = m - h - 1;
+      s1.per[cd] = s2.per[cd] = false;
+      s1.lo[cd] = 0; s1.ext[cd] = 1;
+      s2.lo[cd] = h; s2.ext[cd] = 1;
+      const int a = nd(c1);
+      const int bb = nd(c2);
+      points(s1, sep);
+      points(s2, sep);
+      return add_node(std::move(sep), b, a, bb);
+    }
+    const int mid = b.lo[cd] + b.ext[cd] / 2;
+    c1.ext[cd] = mid - b.lo[cd];
+    c2.lo[cd] = mid + 1;
+    c2.ext[cd] = b.lo[cd] + b.ext[cd] - mid - 1;
+    s1.lo[cd] = mid; s1.ext[cd] = 1;
+    const int a = nd(c1);
+    const int bb = nd(c2);
+    points(s1, sep);
+    return add_node(std::move(sep), b, a, bb);
+  }
+
+  // unknowns coupled to box b through fill: points outside b within distance r (per
+  // non-periodic dimension; periodic dimensions are covered by the box)
+  void halo(const Box& b, std::vector<int>& out) const {
+    int lo[3], ext[3];
+    for (int d = 0; d < 3; ++d) {
+      if (d >= dim) { lo[d] = 0; ext[d] = 1; continue; }
+      if (b.per[d]) { lo[d] = 0; ext[d] = m; }
+      else { lo[d] = b.lo[d] - r; ext[d] = std::min(m, b.ext[d] + 2 * r); }
+    }
+    std::set<int> inside;
+    {
+      std::vector<int> pts;
+      points(b, pts);
+      inside.insert(pts.begin(), pts.end());
+    }
+    std::set<int> seen;
+    for (int tz = 0; tz < ext[2]; ++tz)
+      for (int ty = 0; ty < ext[1]; ++ty)
+        for (int tx = 0; tx < ext[0]; ++tx) {
+          const int p = flat(wrap(lo[0] + tx, m), wrap(lo[1] + ty, m), dim == 3 ? wrap(lo[2] + tz, m) : 0);
+          if (!inside.count(p) && seen.insert(p).second) out.push_back(p);
+        }
+  }
+};
+
+// separable inverse DFT with the 1/n already folded into the input: out[x] = sum_k in[k] e^{+2 pi i k.x/m}
+void idft_separable(int dim, int m, std::vector<cd>& a) {
+  std::vector<cd> tw(m);
+  for (int j = 0; j < m; ++j) tw[j] = cd(std::cos(2.0 * kPi * j / m), std::sin(2.0 * kPi * j / m));
+  std::vector<cd> line(m), res(m);
+  const int n = (dim == 3) ? m * m * m : m * m;
+  for (int axis = 0; axis < dim; ++axis) {
+    const int stride = axis == 0 ? 1 : (axis == 1 ? m : m * m);
+    for (int base = 0; base < n; ++base) {
+      // base must have coordinate 0 along axis
+      const int coord = (base / stride) % m;
+      if (coord != 0) continue;
+      for (int t = 0; t < m; ++t) line[t] = a[base + t * stride];
+      for (int x = 0; x < m; ++x) {
+        cd s(0.0, 0.0);
+        for (int k = 0; k < m; ++k) s += line[k] * tw[(k * x) % m];
+        res[x] = s;
+      }
+      for (int t = 0; t < m; ++t) a[base + t * stride] = res[t];
+    }
+  }
+}
+
+// one-sided Jacobi on the columns of B (rows x cols, column-major); returns V (cols x
+// cols, column-major) with B V having orthogonal columns.
+void one_sided_jacobi(std::vector<cd>& B, int rows, int cols, std::vector<cd>& V) {
+  V.assign((size_t)cols * cols, cd(0.0, 0.0));
+  for (int i = 0; i < cols; ++i) V[(size_t)i * cols + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rotated = false;
+    for (int p = 0; p < cols - 1; ++p)
+      for (int q = p + 1; q < cols; ++q) {
+        cd* bp = &B[(size_t)p * rows];
+        cd* bq = &B[(size_t)q * rows];
+        double al = 0.0, be = 0.0;
+        cd ga(0.0, 0.0);
+        for (int i = 0; i < rows; ++i) {
+          al += std::norm(bp[i]);
+          be += std::norm(bq[i]);
+          ga += std::conj(bp[i]) * bq[i];
+        }
+        const double ag = std::abs(ga);
+        if (ag <= 1e-15 * std::sqrt(al * be) || ag == 0.0) continue;
+        rotated = true;
+        const cd eth = ga / ag;                 // e^{i theta}
+        const double zeta = (be - al) / (2.0 * ag);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        // b_p' = c b_p - s e^{-i th} b_q ; b_q' = s e^{i th} b_p + c b_q
+        const cd sm = s * std::conj(eth), sp = s * eth;
+        for (int i = 0; i < rows; ++i) {
+          const cd x = bp[i], y = bq[i];
+          bp[i] = c * x - sm * y;
+          bq[i] = sp * x + c * y;
+        }
+        cd* vp = &V[(size_t)p * cols];
+        cd* vq = &V[(size_t)q * cols];
+        for (int i = 0; i < cols; ++i) {
+          const cd x = vp[i], y = vq[i];
+          vp[i] = c * x - sm * y;
+          vq[i] = sp * x + c * y;
+        }
+      }
+    if (!rotated) break;
+  }
+}
+
+}  // namespace
+
+SppStructure spp_build_structure(int dim, int m, int r) {
+  SppStructure st;
+  st.dim = dim;
+  st.m = m;
+  st.r = r;
+  st.n = (dim == 3) ? m * m * m : m * m;
+  Builder bd{dim, m, r, &st, {}, {}, {}, {}};
+  Box top;
+  for (int d = 0; d < 3; ++d) {
+    top.lo[d] = 0;
+    top.ext[d] = d < dim ? m : 1;
+    top.per[d] = d < dim;
+  }
+  bd.nd(top);
+  const int nn = (int)bd.node_pts.size();
+  // ND numbering
+  st.perm.clear();
+  st.iperm.assign(st.n, -1);
+  st.nodes.resize(nn);
+  for (int i = 0; i < nn; ++i) {
+    st.nodes[i].off = (int)st.perm.size();
+    st.nodes[i].ns = (int)bd.node_pts[i].size();
+    st.nodes[i].parent = -1;
+    for (int p : bd.node_pts[i]) {
+      st.iperm[p] = (int)st.perm.size();
+      st.perm.push_back(p);
+    }
+  }
+  for (int i = 0; i < nn; ++i) {
+    if (bd.node_children_a[i] >= 0) st.nodes[bd.node_children_a[i]].parent = i;
+    if (bd.node_children_b[i] >= 0) st.nodes[bd.node_children_b[i]].parent = i;
+  }
+  // heights (postorder: children first)
+  for (int i = 0; i < nn; ++i) {
+    int h = 0;
+    if (bd.node_children_a[i] >= 0) h = std::max(h, st.nodes[bd.node_children_a[i]].height + 1);
+    if (bd.node_children_b[i] >= 0) h = std::max(h, st.nodes[bd.node_children_b[i]].height + 1);
+    st.nodes[i].height = h;
+  }
+  // boundaries
+  long long fo = 0;
+  int uo = 0;
+  for (int i = 0; i < nn; ++i) {
+    std::vector<int> hal;
+    bd.halo(bd.node_box[i], hal);
+    std::vector<std::pair<int, int>> b;
+    for (int p : hal) b.push_back({st.iperm[p], p});
+    std::sort(b.begin(), b.end());
+    SppNode& nd = st.nodes[i];
+    nd.nb = (int)b.size();
+    nd.boff = (int)st.bnd.size();
+    for (auto& e : b) {
+      st.bnd.push_back(e.first);
+      st.bnat.push_back(e.second);
+    }
+    nd.uoff = uo;
+    uo += nd.nb;
+    nd.fss = fo;
+    nd.fbs = fo + (long long)nd.ns * nd.ns;
+    nd.fsb = nd.fbs + (long long)nd.nb * nd.ns;
+    fo = nd.fsb + (long long)nd.ns * nd.nb;
+    st.max_ns = std::max(st.max_ns, nd.ns);
+    st.max_nb = std::max(st.max_nb, nd.nb);
+  }
+  st.urows = uo;
+  st.factor_size = fo;
+  // levels
+  int H = 0;
+  for (auto& nd : st.nodes) H = std::max(H, nd.height);
+  st.levels.assign(H + 1, {});
+  for (int i = 0; i < nn; ++i) st.levels[st.nodes[i].height].push_back(i);
+  // contributions: row r receives u[uoff_D + pos] for every node D with bnd_D[pos] = r
+  std::vector<std::vector<int>> rows(st.n);
+  for (int i = 0; i < nn; ++i) {
+    const SppNode& nd = st.nodes[i];
+    for (int pos = 0; pos < nd.nb; ++pos) rows[st.bnd[nd.boff + pos]].push_back(nd.uoff + pos);
+  }
+  st.contrib_ptr.assign(st.n + 1, 0);
+  for (int rr = 0; rr < st.n; ++rr) st.contrib_ptr[rr + 1] = st.contrib_ptr[rr] + (int)rows[rr].size();
+  st.contrib_idx.reserve(st.contrib_ptr[st.n]);
+  for (int rr = 0; rr < st.n; ++rr) st.contrib_idx.insert(st.contrib_idx.end(), rows[rr].begin(), rows[rr].end());
+  // stencil offsets, x fastest
+  const int rz = dim == 3 ? r : 0;
+  for (int dz = -rz; dz <= rz; ++dz)
+    for (int dy = -r; dy <= r; ++dy)
+      for (int dx = -r; dx <= r; ++dx) {
+        st.offsets.push_back(dx);
+        st.offsets.push_back(dy);
+        st.offsets.push_back(dz);
+      }
+  return st;
+}
+
+void green_symbol(int dim, int m, double kin, double lmean, double shift, cd z, std::vector<cd>& ghat) {
+  const int n = (dim == 3) ? m * m * m : m * m;
+  ghat.resize(n);
+  auto sk = [m](int i) { return i < m / 2 ? i : i - m; };
+  for (int i = 0; i < n; ++i) {
+    const int ix = i % m, iy = (i / m) % m, iz = (dim == 3) ? i / (m * m) : 0;
+    const double k2 = (double)sk(ix) * sk(ix) + (double)sk(iy) * sk(iy) + (dim == 3 ? (double)sk(iz) * sk(iz) : 0.0);
+    ghat[i] = 1.0 / (kin * k2 + lmean - shift - z) / (double)n;
+  }
+}
+
+void spp_setup_pole(const SppStructure& st, double kin, const double* V, double shift, cd z, double pivot_floor,
+                    SppPole& out, std::vector<cd>& ghat) {
+  const int dim = st.dim, m = st.m, n = st.n;
+  double lmean = 0.0;
+  for (int i = 0; i < n; ++i) lmean += V[i];
+  lmean /= n;
+  green_symbol(dim, m, kin, lmean, shift, z, ghat);
+  std::vector<cd> g(ghat);
+  idft_separable(dim, m, g);   // g[x] = G(x, 0)
+  const int na = (int)st.offsets.size() / 3;
+  auto off_flat = [&](int dx, int dy, int dz) {
+    return wrap(dx, m) + m * (wrap(dy, m) + (dim == 3 ? m * wrap(dz, m) : 0));
+  };
+  auto coord = [&](int p, int& x, int& y, int& zc) {
+    x = p % m;
+    y = (p / m) % m;
+    zc = dim == 3 ? p / (m * m) : 0;
+  };
+  std::vector<int> a0(na);
+  for (int i = 0; i < na; ++i) a0[i] = off_flat(st.offsets[3 * i], st.offsets[3 * i + 1], st.offsets[3 * i + 2]);
+  std::vector<char> in_a(n, 0);
+  for (int p : a0) in_a[p] = 1;
+  const int rows = n - na;
+  // B = G(a, a^c)^*: column i holds conj(G(o_i, c)) = conj(g[o_i - c]) over c not in a
+  std::vector<cd> B((size_t)na * rows);
+  for (int i = 0; i < na; ++i) {
+    const int ox = st.offsets[3 * i], oy = st.offsets[3 * i + 1], oz = st.offsets[3 * i + 2];
+    int row = 0;
+    for (int c = 0; c < n; ++c) {
+      if (in_a[c]) continue;
+      int cx, cy, cz;
+      coord(c, cx, cy, cz);
+      B[(size_t)i * rows + row] = std::conj(g[off_flat(ox - cx, oy - cy, oz - cz)]);
+      ++row;
+    }
+  }
+  std::vector<cd> Vj;
+  one_sided_jacobi(B, rows, na, Vj);
+  int jmin = 0;
+  double smin = 1e300, smax = 0.0;
+  for (int j = 0; j < na; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < rows; ++i) s += std::norm(B[(size_t)j * rows + i]);
+    s = std::sqrt(s);
+    if (s < smin) { smin = s; jmin = j; }
+    smax = std::max(smax, s);
+  }
+  out.sigma_min = smin;
+  out.sigma_max = smax;
+  out.q.resize(na);
+  for (int i = 0; i < na; ++i) out.q[i] = std::conj(Vj[(size_t)jmin * na + i]);
+  // (qG)(0, a_j) = sum_i q_i G(o_i, o_j) = sum_i q_i g[o_i - o_j]
+  std::vector<cd> qg(na, cd(0.0, 0.0));
+  for (int j = 0; j < na; ++j)
+    for (int i = 0; i < na; ++i)
+      qg[j] += out.q[i] * g[off_flat(st.offsets[3 * i] - st.offsets[3 * j], st.offsets[3 * i + 1] - st.offsets[3 * j + 1],
+                                     st.offsets[3 * i + 2] - st.offsets[3 * j + 2])];
+  // P(row j, stencil t) = q_t + qg_t (V_{j+o_t} - l)
+  auto neighbor = [&](int p, int t) {
+    int x, y, zc;
+    coord(p, x, y, zc);
+    return off_flat(x + st.offsets[3 * t], y + st.offsets[3 * t + 1], zc + st.offsets[3 * t + 2]);
+  };
+  auto pval = [&](int row, int t) { return out.q[t] + qg[t] * (V[neighbor(row, t)] - lmean); };
+  // ---- multifrontal LU
+  out.factor.assign((size_t)st.factor_size, cd(0.0, 0.0));
+  out.pivot_min = 1e300;
+  out.pivot_max = 0.0;
+  out.nperturbed = 0;
+  const int nn = (int)st.nodes.size();
+  std::vector<std::vector<cd>> upd(nn);
+  std::vector<std::vector<int>> children(nn);
+  for (int i = 0; i < nn; ++i)
+    if (st.nodes[i].parent >= 0) children[st.nodes[i].parent].push_back(i);
+  std::vector<int> loc(n, -1);
+  for (int s = 0; s < nn; ++s) {
+    const SppNode& nd = st.nodes[s];
+    const int ns = nd.ns, nb = nd.nb, nf = ns + nb;
+    for (int i = 0; i < ns; ++i) loc[nd.off + i] = i;
+    for (int j = 0; j < nb; ++j) loc[st.bnd[nd.boff + j]] = ns + j;
+    std::vector<cd> F((size_t)nf * nf, cd(0.0, 0.0));
+    for (int i = 0; i < ns; ++i) {
+      const int nat = st.perm[nd.off + i];
+      for (int t = 0; t < na; ++t) {
+        // row entry P(nat, nat + o_t)
+        const int jn = st.iperm[neighbor(nat, t)];
+        if (loc[jn] >= 0) F[(size_t)i * nf + loc[jn]] += pval(nat, t);
+        // column entry P(rnat, nat) where rnat + o_t = nat
+        int x, y, zc;
+        coord(nat, x, y, zc);
+        const int rnat = off_flat(x - st.offsets[3 * t], y - st.offsets[3 * t + 1], zc - st.offsets[3 * t + 2]);
+        const int jr = st.iperm[rnat];
+        if (loc[jr] >= ns) F[(size_t)loc[jr] * nf + i] += pval(rnat, t);
+      }
+    }
+    for (int c : children[s]) {
+      const SppNode& cn = st.nodes[c];
+      const std::vector<cd>& U = upd[c];
+      for (int a = 0; a < cn.nb; ++a) {
+        const int la = loc[st.bnd[cn.boff + a]];
+        for (int b = 0; b < cn.nb; ++b) F[(size_t)la * nf + loc[st.bnd[cn.boff + b]]] += U[(size_t)a * cn.nb + b];
+      }
+      std::vector<cd>().swap(upd[c]);
+    }
+    // partial LU of the first ns rows / columns
+    for (int k = 0; k < ns; ++k) {
+      cd piv = F[(size_t)k * nf + k];
+      double rown = 0.0;
+      for (int j = k; j < nf; ++j) rown = std::max(rown, std::abs(F[(size_t)k * nf + j]));
+      const double ap = std::abs(piv);
+      if (ap < pivot_floor * rown || ap == 0.0) {
+        const double mag = pivot_floor * (rown > 0.0 ? rown : 1.0);
+        piv = (ap > 0.0) ? piv / ap * mag : cd(mag, 0.0);
+        F[(size_t)k * nf + k] = piv;
+        ++out.nperturbed;
+      }
+      out.pivot_min = std::min(out.pivot_min, std::abs(piv));
+      out.pivot_max = std::max(out.pivot_max, std::abs(piv));
+      const cd ip = 1.0 / piv;
+      const cd* rk = &F[(size_t)k * nf];
+      for (int i = k + 1; i < nf; ++i) {
+        cd* ri = &F[(size_t)i * nf];
+        if (ri[k] == cd(0.0, 0.0)) continue;
+        const cd l = ri[k] * ip;
+        ri[k] = l;
+        for (int j = k + 1; j < nf; ++j) ri[j] -= l * rk[j];
+      }
+    }
+    // store blocks; the diagonal of U_SS is stored inverted
+    cd* fss = &out.factor[nd.fss];
+    cd* fbs = &out.factor[nd.fbs];
+    cd* fsb = &out.factor[nd.fsb];
+    for (int i = 0; i < ns; ++i)
+      for (int j = 0; j < ns; ++j) fss[(size_t)i * ns + j] = (i == j) ? 1.0 / F[(size_t)i * nf + j] : F[(size_t)i * nf + j];
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < ns; ++j) fbs[(size_t)i * ns + j] = F[(size_t)(ns + i) * nf + j];
+    for (int i = 0; i < ns; ++i)
+      for (int j = 0; j < nb; ++j) fsb[(size_t)i * nb + j] = F[(size_t)i * nf + ns + j];
+    upd[s].resize((size_t)nb * nb);
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) upd[s][(size_t)i * nb + j] = F[(size_t)(ns + i) * nf + ns + j];
+    for (int i = 0; i < ns; ++i) loc[nd.off + i] = -1;
+    for (int j = 0; j < nb; ++j) loc[st.bnd[nd.boff + j]] = -1;
+  }
+}
+
+}  // namespace omm

@@ -1,0 +1,224 @@
+// Fused pseudospectral kernels: one CTA per grid function, whole grid in shared memory.
+//
+//  happly : Y = F^-1 (T(k) F x) + (V - s_g) x     (Sec. 4 eq. ex1mat; shifted for eq. lst)
+//  greenq : out = Q (F^-1 (Ghat_g(k) F b))          (Sec. 3.2 eqs. GLu / QG: Q (G b))
+//
+// s_g / Ghat_g / q_g depend on the column group g = col / cols_per_group (one group per
+// pole when the columns of all P shifted systems are batched).  T(k) = c |k|^2 with the
+// signed wave numbers k in [-m/2, m/2).
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace omm {
+
+template <typename T, int M, int D>
+struct GridCfg {
+  static constexpr int MX = M, MY = M, MZ = (D == 3 ? M : 1);
+  using LY = fft::Layout<MX, MY, MZ>;
+  static constexpr int N = MX * MY * MZ;
+  static constexpr int NT = (N >= 8192) ? 512 : 256;
+  static constexpr size_t smem = sizeof(cx_t<T>) * (LY::SIZE + M);
+};
+
+template <typename T, int M, int D>
+__global__ void __launch_bounds__(GridCfg<T, M, D>::NT)
+happly_kernel(const cx_t<T>* __restrict__ X, cx_t<T>* __restrict__ Y, const T* __restrict__ V,
+              const double2* __restrict__ shifts, int cols_per_group, const cx_t<T>* __restrict__ tw,
+              double kin_over_n, const int* __restrict__ active) {
+  using C = cx_t<T>;
+  using G = GridCfg<T, M, D>;
+  using LY = typename G::LY;
+  constexpr int NT = G::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  C* t = s + LY::SIZE;
+  const int col = blockIdx.x;
+  if (active && !active[col]) return;
+  const C* x = X + (size_t)col * G::N;
+  for (int i = threadIdx.x; i < M; i += NT) t[i] = tw[i];
+  for (int i = threadIdx.x; i < G::N; i += NT) s[LY::at_flat(i)] = x[i];
+  __syncthreads();
+  fft::transform<-1, LY, G::MZ, NT>(s, t, t, t);
+  const T kc = (T)kin_over_n;
+  for (int i = threadIdx.x; i < G::N; i += NT) {
+    const int ix = i % M, iy = (i / M) % M, iz = i / (M * M);
+    const int kx = fft::signed_k(ix, M), ky = fft::signed_k(iy, M), kz = (D == 3) ? fft::signed_k(iz, M) : 0;
+    const T k2 = (T)(kx * kx + ky * ky + kz * kz);
+    const int a = LY::at_flat(i);
+    s[a] = cscale(s[a], kc * k2);
+  }
+  __syncthreads();
+  fft::transform<+1, LY, G::MZ, NT>(s, t, t, t);
+  const double2 sh = shifts[col / cols_per_group];
+  const T sr = (T)sh.x, si = (T)sh.y;
+  C* y = Y + (size_t)col * G::N;
+  for (int i = threadIdx.x; i < G::N; i += NT) {
+    const C xi = x[i];
+    const T vr = V[i] - sr;
+    // (V - s) x = (vr - i si) x
+    C r = s[LY::at_flat(i)];
+    r.x += vr * xi.x + si * xi.y;
+    r.y += vr * xi.y - si * xi.x;
+    y[i] = r;
+  }
+}
+
+template <typename T, int M, int D>
+__global__ void __launch_bounds__(GridCfg<T, M, D>::NT)
+greenq_kernel(const cx_t<T>* __restrict__ B, cx_t<T>* __restrict__ Out, const cx_t<T>* __restrict__ ghat,
+              const cx_t<T>* __restrict__ q, int nq, int cols_per_group, const cx_t<T>* __restrict__ tw,
+              const int* __restrict__ active) {
+  using C = cx_t<T>;
+  using G = GridCfg<T, M, D>;
+  using LY = typename G::LY;
+  constexpr int NT = G::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  C* t = s + LY::SIZE;
+  __shared__ C qs[27];
+  const int col = blockIdx.x;
+  if (active && !active[col]) return;
+  const int g = col / cols_per_group;
+  const C* b = B + (size_t)col * G::N;
+  for (int i = threadIdx.x; i < M; i += NT) t[i] = tw[i];
+  for (int i = threadIdx.x; i < nq; i += NT) qs[i] = q[(size_t)g * nq + i];
+  for (int i = threadIdx.x; i < G::N; i += NT) s[LY::at_flat(i)] = b[i];
+  __syncthreads();
+  fft::transform<-1, LY, G::MZ, NT>(s, t, t, t);
+  const C* gh = ghat + (size_t)g * G::N;
+  for (int i = threadIdx.x; i < G::N; i += NT) {
+    const int a = LY::at_flat(i);
+    s[a] = cmul(s[a], gh[i]);
+  }
+  __syncthreads();
+  fft::transform<+1, LY, G::MZ, NT>(s, t, t, t);
+  C* o = Out + (size_t)col * G::N;
+  const int r = (nq == 1) ? 0 : 1;   // delta stencil (kinetic inverse only) or the 3^d box
+  for (int i = threadIdx.x; i < G::N; i += NT) {
+    const int ix = i % M, iy = (i / M) % M, iz = i / (M * M);
+    C acc = mk<C>(0, 0);
+    int qi = 0;
+    const int dzr = (D == 3) ? r : 0;
+    for (int dz = -dzr; dz <= dzr; ++dz)
+      for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx, ++qi) {
+          const int xx = (ix + dx + M) % M, yy = (iy + dy + M) % M, zz = (D == 3) ? (iz + dz + M) % M : 0;
+          acc = cfma(qs[qi], s[LY::at(xx, yy, zz)], acc);
+        }
+    o[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- dispatch
+template <typename T, int M, int D>
+static cudaError_t launch_happly_t(const void* X, void* Y, int ncols, const void* V, const double2* shifts,
+                                   int cpg, const void* tw, double kin_over_n, const int* active, cudaStream_t st) {
+  using G = GridCfg<T, M, D>;
+  auto k = happly_kernel<T, M, D>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<ncols, G::NT, G::smem, st>>>((const cx_t<T>*)X, (cx_t<T>*)Y, (const T*)V, shifts, cpg,
+                                   (const cx_t<T>*)tw, kin_over_n, active);
+  return cudaGetLastError();
+}
+
+template <typename T, int M, int D>
+static cudaError_t launch_greenq_t(const void* B, void* Out, int ncols, const void* ghat, const void* q, int nq,
+                                   int cpg, const void* tw, const int* active, cudaStream_t st) {
+  using G = GridCfg<T, M, D>;
+  auto k = greenq_kernel<T, M, D>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<ncols, G::NT, G::smem, st>>>((const cx_t<T>*)B, (cx_t<T>*)Out, (const cx_t<T>*)ghat, (const cx_t<T>*)q, nq,
+                                   cpg, (const cx_t<T>*)tw, active);
+  return cudaGetLastError();
+}
+
+#define OMM_GRID_CASES_2D(X_) X_(8) X_(12) X_(16) X_(24) X_(32) X_(36) X_(48) X_(64) X_(72) X_(96)
+#define OMM_GRID_CASES_3D(X_) X_(4) X_(6) X_(8) X_(12) X_(16)
+
+bool fused_fft_supported(int dim, int m, bool dbl) {
+  if (dim == 2) {
+    switch (m) {
+#define C_(M) case M: return true;
+      OMM_GRID_CASES_2D(C_)
+#undef C_
+      case 128: return !dbl;
+      default: return false;
+    }
+  }
+  if (dim == 3) {
+    switch (m) {
+#define C_(M) case M: return true;
+      OMM_GRID_CASES_3D(C_)
+#undef C_
+      default: return false;
+    }
+  }
+  return false;
+}
+
+cudaError_t launch_happly(bool dbl, int dim, int m, const void* X, void* Y, int ncols, const void* V,
+                          const double2* shifts, int cpg, const void* tw, double kin_over_n, const int* active,
+                          cudaStream_t st) {
+  if (ncols <= 0) return cudaSuccess;
+#define C2_(M)                                                                                        \
+  case M:                                                                                             \
+    return dbl ? launch_happly_t<double, M, 2>(X, Y, ncols, V, shifts, cpg, tw, kin_over_n, active, st)      \
+               : launch_happly_t<float, M, 2>(X, Y, ncols, V, shifts, cpg, tw, kin_over_n, active, st);
+#define C3_(M)                                                                                        \
+  case M:                                                                                             \
+    return dbl ? launch_happly_t<double, M, 3>(X, Y, ncols, V, shifts, cpg, tw, kin_over_n, active, st)      \
+               : launch_happly_t<float, M, 3>(X, Y, ncols, V, shifts, cpg, tw, kin_over_n, active, st);
+  if (dim == 2) {
+    switch (m) {
+      OMM_GRID_CASES_2D(C2_)
+      case 128:
+        if (!dbl) return launch_happly_t<float, 128, 2>(X, Y, ncols, V, shifts, cpg, tw, kin_over_n, active, st);
+        break;
+      default: break;
+    }
+  } else if (dim == 3) {
+    switch (m) { OMM_GRID_CASES_3D(C3_) default: break; }
+  }
+#undef C2_
+#undef C3_
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_greenq(bool dbl, int dim, int m, const void* B, void* Out, int ncols, const void* ghat,
+                          const void* q, int nq, int cpg, const void* tw, const int* active, cudaStream_t st) {
+  if (ncols <= 0) return cudaSuccess;
+#define C2_(M)                                                                                        \
+  case M:                                                                                             \
+    return dbl ? launch_greenq_t<double, M, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st)              \
+               : launch_greenq_t<float, M, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st);
+#define C3_(M)                                                                                        \
+  case M:                                                                                             \
+    return dbl ? launch_greenq_t<double, M, 3>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st)              \
+               : launch_greenq_t<float, M, 3>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st);
+  if (dim == 2) {
+    switch (m) {
+      OMM_GRID_CASES_2D(C2_)
+      case 128:
+        if (!dbl) return launch_greenq_t<float, 128, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st);
+        break;
+      default: break;
+    }
+  } else if (dim == 3) {
+    switch (m) { OMM_GRID_CASES_3D(C3_) default: break; }
+  }
+#undef C2_
+#undef C3_
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace omm

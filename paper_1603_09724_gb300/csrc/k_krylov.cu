@@ -1,0 +1,388 @@
+// Batched restarted GMRES for the P x N shifted systems (H - sigma - z_p) y = b_c of the
+// pole expansion (Sec. 3.1 eqs. direct / lst): right preconditioning, initial guess = the
+// right-hand side, classical Gram-Schmidt with one re-orthogonalisation, Givens rotations
+// on the small Hessenberg matrix, and the preconditioned basis Z kept for the update
+// x += Z y.  One CTA per system for the vector work; one thread per system for the
+// small (m <= 16) dense work.  System s = p * N + c.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace omm {
+
+constexpr int KMAX = 16;   // max basis size (restart m <= 15)
+constexpr int KT = 256;    // threads per system CTA
+
+namespace {
+
+template <int NV>
+__device__ void block_reduce(double (&v)[NV], double* sh) {
+  // sh: >= NV * (KT / 32) doubles; result broadcast to all threads
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q * (KT / 32) + wid] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < KT / 32; ++w) s += sh[q * (KT / 32) + w];
+    v[q] = s;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ cycle start
+template <typename T>
+__global__ void __launch_bounds__(KT) krylov_init_kernel(KrylovDims d, const cx_t<T>* __restrict__ b,
+                                                         const cx_t<T>* __restrict__ Hx, const double2* __restrict__ shifts,
+                                                         cx_t<T>* __restrict__ V0, cx_t<T>* __restrict__ x,
+                                                         double* __restrict__ beta, double2* __restrict__ g,
+                                                         double* __restrict__ bnorm, int* __restrict__ active,
+                                                         double rtol, int fixed, int first) {
+  using C = cx_t<T>;
+  __shared__ double sh[2 * (KT / 32)];
+  const int s = blockIdx.x;
+  const int c = s % d.N, p = s / d.N;
+  const C* bc = b + (size_t)c * d.n;
+  // first cycle: Hx = H0 b_c (one per column), x = b, Ax = H0 b - shift_p b
+  // later cycles: Hx = A x_s (per system)
+  const C* hx = first ? Hx + (size_t)c * d.n : Hx + (size_t)s * d.n;
+  const double2 sh_p = first ? shifts[p] : make_double2(0.0, 0.0);
+  const T sr = (T)sh_p.x, si = (T)sh_p.y;
+  T a0 = 0, a1 = 0;
+  for (size_t i = threadIdx.x; i < d.n; i += KT) {
+    const C bi = bc[i];
+    C r = csub(bi, hx[i]);
+    if (first) {  // + shift * b
+      r.x += sr * bi.x - si * bi.y;
+      r.y += sr * bi.y + si * bi.x;
+      x[(size_t)s * d.n + i] = bi;
+    }
+    a0 += r.x * r.x + r.y * r.y;
+    a1 += bi.x * bi.x + bi.y * bi.y;
+  }
+  double acc[2] = {(double)a0, (double)a1};
+  block_reduce<2>(acc, sh);
+  const double bt = sqrt(acc[0]);
+  const double bn = first ? sqrt(acc[1]) : bnorm[s];
+  const T inv = bt > 0.0 ? (T)(1.0 / bt) : T(0);
+  for (size_t i = threadIdx.x; i < d.n; i += KT) {
+    const C bi = bc[i];
+    C r = csub(bi, hx[i]);
+    if (first) {
+      r.x += sr * bi.x - si * bi.y;
+      r.y += sr * bi.y + si * bi.x;
+    }
+    V0[(size_t)s * d.n + i] = cscale(r, inv);
+  }
+  if (threadIdx.x == 0) {
+    beta[s] = bt;
+    if (first) bnorm[s] = bn;
+    for (int k = 0; k <= d.m; ++k) g[(size_t)s * (KMAX + 1) + k] = make_double2(k == 0 ? bt : 0.0, 0.0);
+    const double rel = bn > 0.0 ? bt / bn : 0.0;
+    active[s] = (bt > 0.0) && (fixed || rel > rtol);
+  }
+}
+
+cudaError_t launch_krylov_init0(bool dbl, KrylovDims d, const void* b, const void* Hb, const double2* shifts, void* V0,
+                                void* x, double* beta, double2* g, double* bnorm, int* active, double rtol, int fixed,
+                                cudaStream_t st) {
+  if (dbl)
+    krylov_init_kernel<double><<<d.S, KT, 0, st>>>(d, (const double2*)b, (const double2*)Hb, shifts, (double2*)V0,
+                                                   (double2*)x, beta, g, bnorm, active, rtol, fixed, 1);
+  else
+    krylov_init_kernel<float><<<d.S, KT, 0, st>>>(d, (const float2*)b, (const float2*)Hb, shifts, (float2*)V0,
+                                                  (float2*)x, beta, g, bnorm, active, rtol, fixed, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_krylov_restart(bool dbl, KrylovDims d, const void* b, const void* Ax, void* V0, double* beta,
+                                  double2* g, const double* bnorm, int* active, double rtol, int fixed,
+                                  cudaStream_t st) {
+  if (dbl)
+    krylov_init_kernel<double><<<d.S, KT, 0, st>>>(d, (const double2*)b, (const double2*)Ax, nullptr,
+                                                   (double2*)V0, nullptr, beta, g, (double*)bnorm, active, rtol,
+                                                   fixed, 0);
+  else
+    krylov_init_kernel<float><<<d.S, KT, 0, st>>>(d, (const float2*)b, (const float2*)Ax, nullptr,
+                                                  (float2*)V0, nullptr, beta, g, (double*)bnorm, active, rtol, fixed,
+                                                  0);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ CGS2
+template <typename T>
+__global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, int k, cx_t<T>* __restrict__ V,
+                                                         const cx_t<T>* __restrict__ w, double2* __restrict__ H,
+                                                         const int* __restrict__ active) {
+  using C = cx_t<T>;
+  __shared__ double sh[2 * KMAX * (KT / 32)];
+  const int s = blockIdx.x;
+  if (!active[s]) return;
+  const size_t n = d.n;
+  const size_t vs = (size_t)d.S * n;   // stride between basis vectors
+  const C* ws = w + (size_t)s * n;
+  const C* Vs = V + (size_t)s * n;
+  double h[2 * KMAX];
+  double h1[2 * KMAX];
+  C ht[KMAX];
+  // pass 1: h1 = V^H w (per-thread partials in the working precision, FP64 across threads)
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q) ht[q] = mk<C>(0, 0);
+  for (size_t i = threadIdx.x; i < n; i += KT) {
+    const C wi = ws[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j <= k) ht[j] = cfmac(Vs[j * vs + i], wi, ht[j]);
+  }
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
+  block_reduce<2 * KMAX>(h, sh);
+#pragma unroll
+  for (int q = 0; q < 2 * KMAX; ++q) h1[q] = h[q];
+  // pass 2: h2 = V^H (w - V h1)
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q) ht[q] = mk<C>(0, 0);
+  for (size_t i = threadIdx.x; i < n; i += KT) {
+    C wi = ws[i];
+    C vv[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j <= k) {
+        vv[j] = Vs[j * vs + i];
+        const C hj = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
+        wi = csub(wi, cmul(hj, vv[j]));
+      }
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j <= k) ht[j] = cfmac(vv[j], wi, ht[j]);
+  }
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
+  block_reduce<2 * KMAX>(h, sh);
+#pragma unroll
+  for (int q = 0; q < 2 * KMAX; ++q) h1[q] += h[q];
+  // pass 3: w'' = w - V (h1 + h2), norm, store into V_{k+1}
+  C* vk1 = V + (size_t)(k + 1) * vs + (size_t)s * n;
+  T nt = 0;
+  for (size_t i = threadIdx.x; i < n; i += KT) {
+    C wi = ws[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j <= k) {
+        const C hj = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
+        wi = csub(wi, cmul(hj, Vs[j * vs + i]));
+      }
+    nt += wi.x * wi.x + wi.y * wi.y;
+    vk1[i] = wi;
+  }
+  double nr[1] = {(double)nt};
+  block_reduce<1>(nr, sh);
+  const double hn = sqrt(nr[0]);
+  const T inv = hn > 0.0 ? (T)(1.0 / hn) : T(0);
+  for (size_t i = threadIdx.x; i < n; i += KT) vk1[i] = cscale(vk1[i], inv);
+  if (threadIdx.x == 0) {
+    double2* Hs = H + (size_t)s * (KMAX + 1) * KMAX;
+    for (int j = 0; j <= k; ++j) Hs[j * KMAX + k] = make_double2(h1[2 * j], h1[2 * j + 1]);
+    Hs[(k + 1) * KMAX + k] = make_double2(hn, 0.0);
+  }
+}
+
+cudaError_t launch_krylov_orth(bool dbl, KrylovDims d, int k, void* V, void* w, double2* H, const int* active,
+                               cudaStream_t st) {
+  if (k + 1 >= KMAX + 1) return cudaErrorInvalidValue;
+  if (dbl)
+    krylov_orth_kernel<double><<<d.S, KT, 0, st>>>(d, k, (double2*)V, (const double2*)w, H, active);
+  else
+    krylov_orth_kernel<float><<<d.S, KT, 0, st>>>(d, k, (float2*)V, (const float2*)w, H, active);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Givens
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+
+__global__ void krylov_givens_kernel(KrylovDims d, int k, double2* __restrict__ H, double2* __restrict__ cs,
+                                     double2* __restrict__ g, const double* __restrict__ bnorm, int* __restrict__ active,
+                                     int* __restrict__ steps, double* __restrict__ est, double rtol, int fixed,
+                                     int* nactive) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.S || !active[s]) return;
+  double2* Hs = H + (size_t)s * (KMAX + 1) * KMAX;
+  double2* css = cs + (size_t)s * KMAX * 2;   // (c as .x, 0) and s complex
+  double2* gs = g + (size_t)s * (KMAX + 1);
+  // apply previous rotations to column k
+  for (int j = 0; j < k; ++j) {
+    const double c = css[2 * j].x;
+    const double2 sn = css[2 * j + 1];
+    const double2 a = Hs[j * KMAX + k], b = Hs[(j + 1) * KMAX + k];
+    const double2 na = make_double2(c * a.x + zmul(sn, b).x, c * a.y + zmul(sn, b).y);
+    const double2 t = zmul(zconj(sn), a);
+    const double2 nb = make_double2(-t.x + c * b.x, -t.y + c * b.y);
+    Hs[j * KMAX + k] = na;
+    Hs[(j + 1) * KMAX + k] = nb;
+  }
+  const double2 a = Hs[k * KMAX + k], b = Hs[(k + 1) * KMAX + k];
+  const double hk1 = zabs(b);
+  const double aa = zabs(a);
+  const double r = hypot(aa, hk1);
+  double c;
+  double2 sn, rr;
+  if (r == 0.0) {
+    c = 1.0; sn = make_double2(0.0, 0.0); rr = make_double2(0.0, 0.0);
+  } else if (aa == 0.0) {
+    c = 0.0; sn = make_double2(1.0, 0.0); rr = b;
+  } else {
+    const double2 al = make_double2(a.x / aa, a.y / aa);
+    c = aa / r;
+    const double2 t = zmul(al, zconj(b));
+    sn = make_double2(t.x / r, t.y / r);
+    rr = make_double2(al.x * r, al.y * r);
+  }
+  css[2 * k] = make_double2(c, 0.0);
+  css[2 * k + 1] = sn;
+  Hs[k * KMAX + k] = rr;
+  Hs[(k + 1) * KMAX + k] = make_double2(0.0, 0.0);
+  const double2 gk = gs[k];
+  gs[k] = make_double2(c * gk.x, c * gk.y);
+  const double2 t = zmul(zconj(sn), gk);
+  gs[k + 1] = make_double2(-t.x, -t.y);
+  steps[s] = k + 1;
+  const double e = zabs(gs[k + 1]) / (bnorm[s] > 0.0 ? bnorm[s] : 1.0);
+  est[s] = e;
+  const bool done = (hk1 == 0.0) || (!fixed && e <= rtol);
+  if (done) active[s] = 0;
+  else atomicAdd(nactive, 1);
+}
+
+cudaError_t launch_krylov_givens(KrylovDims d, int k, double2* H, double2* cs, double2* g, const double* bnorm,
+                                 int* active, int* steps, double* est, double rtol, int fixed, int* nactive,
+                                 cudaStream_t st) {
+  krylov_givens_kernel<<<(d.S + 127) / 128, 128, 0, st>>>(d, k, H, cs, g, bnorm, active, steps, est, rtol, fixed,
+                                                          nactive);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ solution update
+__global__ void krylov_backsolve_kernel(KrylovDims d, const double2* __restrict__ H, const double2* __restrict__ g,
+                                        const int* __restrict__ steps, double2* __restrict__ y, int* itot) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.S) return;
+  const int k = steps[s];
+  itot[s] += k;
+  const double2* Hs = H + (size_t)s * (KMAX + 1) * KMAX;
+  const double2* gs = g + (size_t)s * (KMAX + 1);
+  double2* ys = y + (size_t)s * KMAX;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 acc = gs[i];
+    for (int j = i + 1; j < k; ++j) {
+      const double2 p = zmul(Hs[i * KMAX + j], ys[j]);
+      acc.x -= p.x;
+      acc.y -= p.y;
+    }
+    const double2 dg = Hs[i * KMAX + i];
+    const double den = dg.x * dg.x + dg.y * dg.y;
+    ys[i] = den > 0.0 ? make_double2((acc.x * dg.x + acc.y * dg.y) / den, (acc.y * dg.x - acc.x * dg.y) / den)
+                      : make_double2(0.0, 0.0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(KT) krylov_xupdate_kernel(KrylovDims d, const int* __restrict__ steps,
+                                                            const double2* __restrict__ y, const cx_t<T>* __restrict__ Z,
+                                                            cx_t<T>* __restrict__ x) {
+  using C = cx_t<T>;
+  const int s = blockIdx.x;
+  const int k = steps[s];
+  if (k == 0) return;
+  const size_t n = d.n, vs = (size_t)d.S * n;
+  C yy[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    const double2 v = j < k ? y[(size_t)s * KMAX + j] : make_double2(0.0, 0.0);
+    yy[j] = mk<C>((T)v.x, (T)v.y);
+  }
+  const C* Zs = Z + (size_t)s * n;
+  C* xs = x + (size_t)s * n;
+  for (size_t i = threadIdx.x; i < n; i += KT) {
+    C acc = xs[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) acc = cfma(yy[j], Zs[j * vs + i], acc);
+    xs[i] = acc;
+  }
+}
+
+cudaError_t launch_krylov_update(bool dbl, KrylovDims d, const double2* H, const double2* g, const int* steps,
+                                 double2* y, const void* Z, void* x, int* itot, cudaStream_t st) {
+  krylov_backsolve_kernel<<<(d.S + 127) / 128, 128, 0, st>>>(d, H, g, steps, y, itot);
+  if (dbl)
+    krylov_xupdate_kernel<double><<<d.S, KT, 0, st>>>(d, steps, y, (const double2*)Z, (double2*)x);
+  else
+    krylov_xupdate_kernel<float><<<d.S, KT, 0, st>>>(d, steps, y, (const float2*)Z, (float2*)x);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pole combination
+template <typename T>
+__global__ void pole_combine_kernel(KrylovDims d, int P, const double2* __restrict__ w, double sign,
+                                    const cx_t<T>* __restrict__ x, cx_t<T>* __restrict__ out) {
+  using C = cx_t<T>;
+  const size_t total = (size_t)d.N * d.n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = e / d.n, i = e % d.n;
+    C acc = mk<C>(0, 0);
+    for (int p = 0; p < P; ++p) {
+      const double2 wp = w[p];
+      const C wc = mk<C>((T)(sign * wp.x), (T)(sign * wp.y));
+      acc = cfma(wc, x[((size_t)p * d.N + c) * d.n + i], acc);
+    }
+    out[e] = acc;
+  }
+}
+
+cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w, double sign, const void* x, void* out,
+                                cudaStream_t st) {
+  const size_t total = (size_t)d.N * d.n;
+  const int blocks = (int)((total + 255) / 256 < 4864 ? (total + 255) / 256 : 4864);
+  if (dbl)
+    pole_combine_kernel<double><<<blocks, 256, 0, st>>>(d, P, w, sign, (const double2*)x, (double2*)out);
+  else
+    pole_combine_kernel<float><<<blocks, 256, 0, st>>>(d, P, w, sign, (const float2*)x, (float2*)out);
+  return cudaGetLastError();
+}
+
+__global__ void count_active_kernel(KrylovDims d, const int* __restrict__ active, int* nactive) {
+  __shared__ int sh;
+  if (threadIdx.x == 0) sh = 0;
+  __syncthreads();
+  int c = 0;
+  for (int s = threadIdx.x; s < d.S; s += blockDim.x) c += active[s] ? 1 : 0;
+  atomicAdd(&sh, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *nactive = sh;
+}
+
+cudaError_t launch_count_active(KrylovDims d, const int* active, int* nactive, cudaStream_t st) {
+  count_active_kernel<<<1, 1024, 0, st>>>(d, active, nactive);
+  return cudaGetLastError();
+}
+
+__global__ void krylov_reset_kernel(KrylovDims d, int* active, int* steps) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < d.S) { active[s] = 1; steps[s] = 0; }
+}
+
+cudaError_t launch_krylov_reset(KrylovDims d, int* active, int* steps, cudaStream_t st) {
+  krylov_reset_kernel<<<(d.S + 255) / 256, 256, 0, st>>>(d, active, steps);
+  return cudaGetLastError();
+}
+
+}  // namespace omm

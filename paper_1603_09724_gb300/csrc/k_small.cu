@@ -1,0 +1,221 @@
+// N x N algebra in FP64 on one CTA: quartic coefficients of E_omm(X + tD), the exact
+// line search, energies, the Grams of the updated X, and the Polak-Ribiere beta.
+//
+// eq. omm: E(X) = 1/2 tr((2I - X^*X)(X^*HX)).  With S(t) = A + tB + t^2 C and
+// K(t) = A_H + t B_H + t^2 C_H (A = X^*X, B = X^*D + D^*X, C = D^*D and the same with H)
+// E(t) = tr K(t) - 1/2 tr(S(t) K(t)) = c0 + c1 t + ... + c4 t^4.  The minimiser over real
+// t is one of the real roots of E'(t) (a cubic); c4 = -1/2 tr(C C_H) > 0 for H < 0.
+// H = H0 - sigma: the Grams come from the unshifted H0 X (so that no large shift enters
+// the working-precision data) and sigma is applied here in FP64.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace omm {
+
+namespace {
+
+__device__ double cubic_value(const double* a, double t) { return ((a[3] * t + a[2]) * t + a[1]) * t + a[0]; }
+__device__ double cubic_deriv(const double* a, double t) { return (3.0 * a[3] * t + 2.0 * a[2]) * t + a[1]; }
+
+// Real roots of a[3] t^3 + a[2] t^2 + a[1] t + a[0] (a[3] != 0); returns the count.
+// Depressed cubic y^3 + P y + Q = 0 with t = y - p2/3; Cardano for one real root,
+// the trigonometric form for three; each root is refined by Newton steps.
+__device__ int cubic_real_roots(const double* a, double* r) {
+  const double p2 = a[2] / a[3], p1 = a[1] / a[3], p0 = a[0] / a[3];
+  const double P = p1 - p2 * p2 / 3.0;
+  const double Q = 2.0 * p2 * p2 * p2 / 27.0 - p2 * p1 / 3.0 + p0;
+  const double disc = 0.25 * Q * Q + P * P * P / 27.0;
+  int nr = 0;
+  if (disc > 0.0) {
+    const double sq = sqrt(disc);
+    const double u = cbrt(-0.5 * Q - copysign(sq, Q));
+    const double y = (u != 0.0) ? u - P / (3.0 * u) : 0.0;
+    r[nr++] = y - p2 / 3.0;
+  } else if (P == 0.0) {
+    r[nr++] = -p2 / 3.0;
+  } else {
+    const double mP = -P / 3.0;
+    const double rad = sqrt(mP);
+    double arg = -0.5 * Q / (mP * rad);
+    arg = fmax(-1.0, fmin(1.0, arg));
+    const double phi = acos(arg);
+    const double twopi3 = 2.0943951023931954923084289221863353;  // 2 pi / 3
+    for (int k = 0; k < 3; ++k) r[nr++] = 2.0 * rad * cos(phi / 3.0 - twopi3 * k) - p2 / 3.0;
+  }
+  for (int i = 0; i < nr; ++i) {
+    double t = r[i];
+    for (int it = 0; it < 4; ++it) {
+      const double d = cubic_deriv(a, t);
+      if (d == 0.0) break;
+      const double step = cubic_value(a, t) / d;
+      t -= step;
+      if (fabs(step) <= 1e-16 * fabs(t)) break;
+    }
+    r[i] = t;
+  }
+  return nr;
+}
+
+__device__ double quartic(const double* c, double t) { return c[0] + t * (c[1] + t * (c[2] + t * (c[3] + t * c[4]))); }
+
+template <int NV>
+__device__ void block_sum_vec(double (&v)[NV], double* sh /* >= 32 * NV */) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wid * NV + q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += sh[w * NV + q];
+      v[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(1024) line_search_kernel(const double2* __restrict__ Cg, int N, double sigma,
+                                                           int have_d, double tol, OmmScalars* sc,
+                                                           cx_t<T>* __restrict__ M1, cx_t<T>* __restrict__ M2) {
+  __shared__ double sh[32 * 12];
+  __shared__ double t_sh;
+  const int ld = 4 * N;
+  auto at = [&](int r, int c) { return Cg[(size_t)r * ld + c]; };
+  // shifted blocks as functions of (i, j)
+  auto A = [&](int i, int j) { return at(i, j); };
+  auto Bm = [&](int i, int j) {
+    double2 a = at(i, N + j), b = at(N + i, j);
+    return make_double2(a.x + b.x, a.y + b.y);
+  };
+  auto Cm = [&](int i, int j) { return at(N + i, N + j); };
+  auto AH = [&](int i, int j) {
+    double2 h = at(i, 2 * N + j), s = at(i, j);
+    return make_double2(h.x - sigma * s.x, h.y - sigma * s.y);
+  };
+  auto BH = [&](int i, int j) {
+    double2 h1 = at(i, 3 * N + j), h2 = at(N + i, 2 * N + j);
+    double2 s = Bm(i, j);
+    return make_double2(h1.x + h2.x - sigma * s.x, h1.y + h2.y - sigma * s.y);
+  };
+  auto CH = [&](int i, int j) {
+    double2 h = at(N + i, 3 * N + j), s = at(N + i, N + j);
+    return make_double2(h.x - sigma * s.x, h.y - sigma * s.y);
+  };
+  auto rmul = [](double2 p, double2 q) { return p.x * q.x - p.y * q.y; };  // Re(p q)
+  // v: 0 trAH, 1 trBH, 2 trCH, 3 tr(A AH), 4 tr(A BH), 5 tr(B AH), 6 tr(A CH), 7 tr(B BH),
+  //    8 tr(C AH), 9 tr(B CH), 10 tr(C BH), 11 tr(C CH)
+  double v[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) v[q] = 0.0;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    const double2 a_ij = A(i, j), ah_ji = AH(j, i);
+    if (i == j) v[0] += ah_ji.x;
+    v[3] += rmul(a_ij, ah_ji);
+    if (have_d) {
+      const double2 b_ij = Bm(i, j), c_ij = Cm(i, j);
+      const double2 bh_ji = BH(j, i), ch_ji = CH(j, i);
+      if (i == j) { v[1] += bh_ji.x; v[2] += ch_ji.x; }
+      v[4] += rmul(a_ij, bh_ji);
+      v[5] += rmul(b_ij, ah_ji);
+      v[6] += rmul(a_ij, ch_ji);
+      v[7] += rmul(b_ij, bh_ji);
+      v[8] += rmul(c_ij, ah_ji);
+      v[9] += rmul(b_ij, ch_ji);
+      v[10] += rmul(c_ij, bh_ji);
+      v[11] += rmul(c_ij, ch_ji);
+    }
+  }
+  block_sum_vec<12>(v, sh);
+  if (threadIdx.x == 0) {
+    double c[5];
+    c[0] = v[0] - 0.5 * v[3];
+    c[1] = v[1] - 0.5 * (v[4] + v[5]);
+    c[2] = v[2] - 0.5 * (v[6] + v[7] + v[8]);
+    c[3] = -0.5 * (v[9] + v[10]);
+    c[4] = -0.5 * v[11];
+    double t = 0.0;
+    int bad = 0;
+    if (have_d) {
+      if (!(c[4] > 0.0)) {
+        bad = 1;
+      } else {
+        double a[4] = {c[1], 2.0 * c[2], 3.0 * c[3], 4.0 * c[4]};
+        double r[3];
+        const int nr = cubic_real_roots(a, r);
+        double best = quartic(c, r[0]);
+        t = r[0];
+        for (int i = 1; i < nr; ++i) {
+          const double e = quartic(c, r[i]);
+          const double tie = 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(best));
+          if (e < best - tie || (fabs(e - best) <= tie && fabs(r[i]) < fabs(t))) {
+            best = e;
+            t = r[i];
+          }
+        }
+      }
+    }
+    for (int q = 0; q < 5; ++q) sc->c[q] = c[q];
+    sc->t = t;
+    sc->t_c = make_double2(t, 0.0);
+    sc->one_c = make_double2(1.0, 0.0);
+    sc->E0 = c[0];
+    sc->E1 = quartic(c, t);
+    sc->bad = bad;
+    sc->converged = fabs(sc->E1 - sc->E0) <= tol * fabs(sc->E1);
+    t_sh = t;
+  }
+  __syncthreads();
+  const double t = t_sh;
+  // Grams of X + tD (unshifted K0), then M1 = -(K0 + 2 sigma (I - S)), M2 = -S
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    double2 S = A(i, j);
+    double2 K0 = at(i, 2 * N + j);
+    if (have_d) {
+      const double2 b = Bm(i, j), cc = Cm(i, j);
+      const double2 h1 = at(i, 3 * N + j), h2 = at(N + i, 2 * N + j), hd = at(N + i, 3 * N + j);
+      S.x += t * b.x + t * t * cc.x;
+      S.y += t * b.y + t * t * cc.y;
+      K0.x += t * (h1.x + h2.x) + t * t * hd.x;
+      K0.y += t * (h1.y + h2.y) + t * t * hd.y;
+    }
+    const double id = (i == j) ? 1.0 : 0.0;
+    const double m1r = -(K0.x + 2.0 * sigma * (id - S.x));
+    const double m1i = -(K0.y - 2.0 * sigma * S.y);
+    M1[idx] = mk<cx_t<T>>((T)m1r, (T)m1i);
+    M2[idx] = mk<cx_t<T>>((T)(-S.x), (T)(-S.y));
+  }
+}
+
+cudaError_t launch_line_search(bool dbl, const double2* C, int N, double sigma, int have_d, double tol,
+                               OmmScalars* sc, void* M1, void* M2, cudaStream_t st) {
+  if (dbl)
+    line_search_kernel<double><<<1, 1024, 0, st>>>(C, N, sigma, have_d, tol, sc, (double2*)M1, (double2*)M2);
+  else
+    line_search_kernel<float><<<1, 1024, 0, st>>>(C, N, sigma, have_d, tol, sc, (float2*)M1, (float2*)M2);
+  return cudaGetLastError();
+}
+
+__global__ void pr_beta_kernel(OmmScalars* sc, int first) {
+  double beta = 0.0;
+  if (!first && sc->ggp != 0.0) beta = (sc->gg - sc->gdot) / sc->ggp;
+  sc->beta = beta;
+  sc->beta_c = make_double2(beta, 0.0);
+  sc->ggp = sc->gg;
+}
+
+cudaError_t launch_pr_beta(OmmScalars* sc, int first, cudaStream_t st) {
+  pr_beta_kernel<<<1, 1, 0, st>>>(sc, first);
+  return cudaGetLastError();
+}
+
+}  // namespace omm

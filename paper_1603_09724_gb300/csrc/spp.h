@@ -1,0 +1,63 @@
+// Host-side setup of the sparsifying preconditioner (Sec. 3.2): the stencil row q of
+// eq. QG, the sparse matrix P of eq. P, a nested-dissection ordering of the periodic
+// grid and the multifrontal LU factorisation of P (dense supernodes), laid out for the
+// device triangular solves.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+namespace omm {
+
+using cd = std::complex<double>;
+
+struct SppNode {
+  int off;      // first ND index of the supernode's unknowns
+  int ns;       // number of unknowns (separator or leaf box)
+  int nb;       // boundary size |B(s)| (ancestor unknowns coupled to the subtree)
+  int boff;     // offset into SppStructure::bnat / bnd
+  int uoff;     // first row of this node's update vector in the u buffer
+  long long fss, fbs, fsb;   // offsets of the dense blocks in a pole's factor array
+  int parent;   // parent node (-1 at the root)
+  int height;   // 0 for leaves
+};
+
+struct SppStructure {
+  int dim = 0, m = 0, r = 1;
+  int n = 0;
+  std::vector<int> perm;      // perm[nd] = natural index of ND unknown nd
+  std::vector<int> iperm;     // iperm[natural] = ND index
+  std::vector<SppNode> nodes; // postorder
+  std::vector<int> bnat;      // boundary unknowns (natural indices), per node
+  std::vector<int> bnd;       // same, ND indices (sorted ascending per node)
+  std::vector<std::vector<int>> levels;  // node ids per height
+  std::vector<int> contrib_ptr;  // CSR over ND rows: contributions u-row indices
+  std::vector<int> contrib_idx;
+  int urows = 0;               // total rows of update vectors
+  long long factor_size = 0;   // complex entries per pole
+  int max_ns = 0, max_nb = 0;
+  std::vector<int> offsets;    // stencil offsets, flattened (dx, dy, dz) triples, x fastest
+};
+
+struct SppPole {
+  std::vector<cd> q;            // stencil row (|a| entries, same order as offsets)
+  std::vector<cd> factor;       // dense blocks, per node: L\U of S (ns x ns, row-major),
+                                // L_BS (nb x ns row-major), U_SB (ns x nb row-major)
+  double pivot_min = 0, pivot_max = 0;
+  int nperturbed = 0;
+  double sigma_min = 0, sigma_max = 0;   // singular values of G(a, a^c)
+};
+
+// Builds the ND structure for an m^dim periodic grid and stencil radius r.
+SppStructure spp_build_structure(int dim, int m, int r);
+
+// Per pole: q by the SVD of G(a, a^c), P assembly, multifrontal LU with static pivoting.
+// kin: (2 pi^2 / L^2); V: n reals; shift: sigma; z: pole.  ghat_out (n) receives
+// 1/(T(k) + l - sigma - z) / n (the Green symbol with the inverse-DFT scale folded in).
+void spp_setup_pole(const SppStructure& st, double kin, const double* V, double shift, cd z, double pivot_floor,
+                    SppPole& out, std::vector<cd>& ghat_out);
+
+// Green symbol only (for the kinetic inner preconditioner).
+void green_symbol(int dim, int m, double kin, double lmean, double shift, cd z, std::vector<cd>& ghat_out);
+
+}  // namespace omm

@@ -1,0 +1,40 @@
+// Device-side description of the nested-dissection multifrontal factor structure.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <vector>
+
+namespace omm {
+
+struct TrsvArgs {
+  // per node (device arrays)
+  const int* node_ns;
+  const int* node_nb;
+  const int* node_off;
+  const int* node_boff;
+  const int* node_uoff;
+  const long long* node_fss;
+  const long long* node_fbs;
+  const long long* node_fsb;
+  const int* perm;          // ND -> natural
+  const int* bnat;          // boundary natural indices
+  const int* contrib_ptr;   // n + 1
+  const int* contrib_idx;
+  long long factor_size;    // complex entries per pole
+  size_t n;                 // grid points
+  int N;                    // right-hand sides per pole
+  size_t S;                 // total systems (rows stride of the u buffer)
+};
+
+struct TrsvLevels {
+  int nlevels;
+  const int* nodes;               // device: node ids grouped by height
+  std::vector<int> start, count;  // host
+};
+
+size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb);
+// b (natural, S systems) -> x (natural); ynd, u work buffers.  factor: P poles' blocks.
+cudaError_t launch_spp_solve(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, int P, const void* b, void* ynd,
+                             void* u, void* x, const void* factor, const int* active, size_t smem, cudaStream_t st);
+
+}  // namespace omm

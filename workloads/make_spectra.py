@@ -1,0 +1,52 @@
+"""Writes workloads/spectra.json: the spectral data of each workload's H - sigma computed by
+the oracle only (dense eigh for n <= 4096, the truncated plane-wave basis of
+oracle.spectrum otherwise).
+
+The pole rule needs the occupied interval [lam_1, lam_N] and lam_{N+1}; the paper builds
+its contour from the exact spectrum (Sec. 4), so the workloads carry these stored
+values.  E_ref = 1/2 sum_{i<=N} lam_i is the exact minimum of E_omm (Sec. 1).
+
+Run: python -m workloads.make_spectra
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from oracle import hamiltonian as ham
+from oracle import spectrum
+from workloads import WORKLOADS
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "spectra.json")
+
+
+def compute(wl, kc=24):
+    V = wl.potential_values()
+    shape = wl.shape
+    sig = ham.default_shift(shape, wl.L, V)
+    if wl.n <= 4096:
+        lam = np.linalg.eigvalsh(ham.dense_h(shape, wl.L, V, sig))[: wl.N + 8]
+        how = "dense eigh"
+    else:
+        lam = spectrum.lowest_eigs_kspace(shape, wl.L, V, sig, wl.N + 8, kc)
+        how = f"plane-wave box |k|_inf <= {kc}"
+    lo, hi = ham.weyl_bounds(shape, wl.L, V, sig)
+    return dict(sigma=sig, lam1=float(lam[0]), lamN=float(lam[wl.N - 1]), lamN1=float(lam[wl.N]),
+                weyl_lo=lo, weyl_hi=hi, E_ref=float(0.5 * np.sum(lam[: wl.N])), method=how,
+                lowest=[float(x) for x in lam])
+
+
+def main(names=("wells2d-32", "smooth2d-128")):
+    data = {}
+    if os.path.exists(OUT):
+        data = json.load(open(OUT))
+    for name in names:
+        data[name] = compute(WORKLOADS[name])
+        print(name, data[name]["lamN1"] - data[name]["lamN"], data[name]["method"])
+    json.dump(data, open(OUT, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main()

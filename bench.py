@@ -38,6 +38,10 @@ def args_parse():
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the untimed FP64-form comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", type=int, default=1, help="per-kernel CUDA-event timing in the timed region")
+    ap.add_argument("--refilter", type=int, default=0, help="extra filter + CG rounds after convergence")
+    ap.add_argument("--rtol", type=float, default=1e-5, help="GMRES relative tolerance (paper: 1e-5)")
+    ap.add_argument("--N", type=int, default=0, help="override N (reduced case for profiler captures only)")
+    ap.add_argument("--P", type=int, default=0, help="override P (reduced case for profiler captures only)")
     return ap.parse_args()
 
 
@@ -101,12 +105,13 @@ def load_workload(name):
     return wl, spectra
 
 
-def workload_config(wl, spectra, iters, precision="mixed"):
+def workload_config(wl, spectra, iters, precision="mixed", refilter=0, rtol=1e-5):
     return {"workload": f"{wl.name}: {wl.dim}D {wl.m}^{wl.dim} periodic grid (n={wl.n}), N={wl.N} states, "
                         f"P={wl.P} conformal poles, {wl.potential} potential, {precision}",
             "grid": [wl.m] * wl.dim, "box_len": wl.L, "N": wl.N, "P": wl.P, "precision": precision,
             "inner_preconditioner": "sparsifying (nested-dissection multifrontal LU)",
-            "gmres": "restart 15, <=5 cycles, rtol 1e-5", "cg_iters": iters if iters else "energy criterion",
+            "gmres": f"restart 15, <=5 cycles, rtol {rtol:g}", "cg_iters": iters if iters else "energy criterion",
+            "refilter": refilter,
             "l2": "inputs/working set larger than L2 (GMRES basis ~GBs)", "parallelism": "replicas",
             "spectral_interval": "stored exact [lam_1, lam_N], lam_{N+1} (workloads/spectra.json)"}
 
@@ -192,6 +197,9 @@ def run_ours(a):
     import paper_1603_09724_gb300 as omm
 
     wl, spectra = load_workload(a.workload)
+    if a.N or a.P:
+        import dataclasses
+        wl = dataclasses.replace(wl, N=a.N or wl.N, P=a.P or wl.P)
     V = wl.potential_values()
     mixed = wl.precision == "mixed"
     prec = omm.OMM_MIXED if mixed else omm.OMM_FP64
@@ -199,7 +207,7 @@ def run_ours(a):
     z, w = omm.poles_fermi(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
     tol = 0.0 if a.iters else (1e-10 if mixed else 1e-13)
     maxit = a.iters if a.iters else 40
-    prm = omm.default_params(precision=prec, maxit=maxit, tol=tol)
+    prm = omm.default_params(precision=prec, maxit=maxit, tol=tol, refilter=a.refilter, gmres_rtol=a.rtol)
     s = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
     t_setup = time.perf_counter()
     s.set_poles(z, w)
@@ -273,7 +281,7 @@ def run_ours(a):
     rec = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64" if mixed else "c128", "data": "synthetic",
-           "config": workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64"),
+           "config": workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64", a.refilter, a.rtol),
            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
            "solve": {"iters": st["iters"], "filters": st["filters"], "converged": st["converged"],
                      "energy_fp64": st["energy_fp64"], "resid_fp64": st["resid_fp64"],

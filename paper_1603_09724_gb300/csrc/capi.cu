@@ -141,14 +141,14 @@ struct omm_ctx {
   int* d_node_off = nullptr;
   int* d_node_boff = nullptr;
   int* d_node_uoff = nullptr;
-  long long* d_node_fss = nullptr;
-  long long* d_node_fbs = nullptr;
-  long long* d_node_fsb = nullptr;
+  long long* d_node_wf = nullptr;
+  long long* d_node_wb = nullptr;
   int* d_perm = nullptr;
   int* d_bnat = nullptr;
   int* d_cptr = nullptr;
   int* d_cidx = nullptr;
-  int* d_levels = nullptr;
+  int* d_fblocks = nullptr;
+  int* d_bblocks = nullptr;
   size_t trsv_smem = 0;
   int last_gmres_max = 0;
   double last_relres_max = 0.0;
@@ -395,9 +395,8 @@ TrsvArgs trsv_args(omm_ctx* h, int Ncols, size_t S) {
   a.node_off = h->d_node_off;
   a.node_boff = h->d_node_boff;
   a.node_uoff = h->d_node_uoff;
-  a.node_fss = h->d_node_fss;
-  a.node_fbs = h->d_node_fbs;
-  a.node_fsb = h->d_node_fsb;
+  a.node_wf = h->d_node_wf;
+  a.node_wb = h->d_node_wb;
   a.perm = h->d_perm;
   a.bnat = h->d_bnat;
   a.contrib_ptr = h->d_cptr;
@@ -412,13 +411,14 @@ TrsvArgs trsv_args(omm_ctx* h, int Ncols, size_t S) {
 TrsvLevels trsv_levels(omm_ctx* h) {
   TrsvLevels lv;
   lv.nlevels = (int)h->spp.levels.size();
-  lv.nodes = h->d_levels;
-  int s = 0;
-  for (auto& l : h->spp.levels) {
-    lv.start.push_back(s);
-    lv.count.push_back((int)l.size());
-    s += (int)l.size();
-  }
+  lv.fblocks = h->d_fblocks;
+  lv.bblocks = h->d_bblocks;
+  lv.fstart = h->spp.fstart;
+  lv.fcount = h->spp.fcount;
+  lv.bstart = h->spp.bstart;
+  lv.bcount = h->spp.bcount;
+  lv.fkmax = h->spp.fkmax;
+  lv.bkmax = h->spp.bkmax;
   return lv;
 }
 
@@ -434,7 +434,9 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   TrsvArgs a = trsv_args(h, Ncols, S);
   TrsvLevels lv = trsv_levels(h);
   const double bytes = ((double)P * h->spp.factor_size + (4.0 * h->n + 2.0 * h->spp.urows) * (double)S) * h->csz;
-  PROF(PC_TRSV, bytes, 2 * lv.nlevels,
+  int nk = 0;
+  for (int l = 0; l < lv.nlevels; ++l) nk += (lv.fcount[l] > 0) + (lv.bcount[l] > 0);
+  PROF(PC_TRSV, bytes, nk,
        cuda_status(launch_spp_solve(h->dbl, a, lv, P, tmp, h->ynd, h->ubuf, Z, h->factor, active, h->trsv_smem, h->st),
                    "spp"));
   return OMM_OK;
@@ -694,26 +696,25 @@ omm_status build_spp(omm_ctx* h) {
     const SppStructure& s = h->spp;
     h->trsv_smem = trsv_smem_bytes(h->dbl, s.max_ns, s.max_nb);
     if (h->trsv_smem > 220 * 1024) return OMM_EUNSUPPORTED;
-    std::vector<int> ns, nb, off, boff, uoff, lev;
-    std::vector<long long> fss, fbs, fsb;
+    std::vector<int> ns, nb, off, boff, uoff;
+    std::vector<long long> wf, wb;
     for (auto& nd : s.nodes) {
       ns.push_back(nd.ns); nb.push_back(nd.nb); off.push_back(nd.off); boff.push_back(nd.boff);
-      uoff.push_back(nd.uoff); fss.push_back(nd.fss); fbs.push_back(nd.fbs); fsb.push_back(nd.fsb);
+      uoff.push_back(nd.uoff); wf.push_back(nd.wf); wb.push_back(nd.wb);
     }
-    for (auto& l : s.levels) lev.insert(lev.end(), l.begin(), l.end());
     OMM_TRY(upload_vec(h, &h->d_node_ns, ns));
     OMM_TRY(upload_vec(h, &h->d_node_nb, nb));
     OMM_TRY(upload_vec(h, &h->d_node_off, off));
     OMM_TRY(upload_vec(h, &h->d_node_boff, boff));
     OMM_TRY(upload_vec(h, &h->d_node_uoff, uoff));
-    OMM_TRY(upload_vec(h, &h->d_node_fss, fss));
-    OMM_TRY(upload_vec(h, &h->d_node_fbs, fbs));
-    OMM_TRY(upload_vec(h, &h->d_node_fsb, fsb));
+    OMM_TRY(upload_vec(h, &h->d_node_wf, wf));
+    OMM_TRY(upload_vec(h, &h->d_node_wb, wb));
     OMM_TRY(upload_vec(h, &h->d_perm, s.perm));
     OMM_TRY(upload_vec(h, &h->d_bnat, s.bnat));
     OMM_TRY(upload_vec(h, &h->d_cptr, s.contrib_ptr));
     OMM_TRY(upload_vec(h, &h->d_cidx, s.contrib_idx));
-    OMM_TRY(upload_vec(h, &h->d_levels, lev));
+    OMM_TRY(upload_vec(h, &h->d_fblocks, s.fblocks));
+    OMM_TRY(upload_vec(h, &h->d_bblocks, s.bblocks));
     OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
     h->spp_built = true;
   }

@@ -257,10 +257,9 @@ SppStructure spp_build_structure(int dim, int m, int r) {
     }
     nd.uoff = uo;
     uo += nd.nb;
-    nd.fss = fo;
-    nd.fbs = fo + (long long)nd.ns * nd.ns;
-    nd.fsb = nd.fbs + (long long)nd.nb * nd.ns;
-    fo = nd.fsb + (long long)nd.ns * nd.nb;
+    nd.wf = fo;
+    nd.wb = fo + (long long)(nd.ns + nd.nb) * nd.ns;
+    fo = nd.wb + (long long)nd.ns * (nd.ns + nd.nb);
     st.max_ns = std::max(st.max_ns, nd.ns);
     st.max_nb = std::max(st.max_nb, nd.nb);
   }
@@ -271,6 +270,24 @@ SppStructure spp_build_structure(int dim, int m, int r) {
   for (auto& nd : st.nodes) H = std::max(H, nd.height);
   st.levels.assign(H + 1, {});
   for (int i = 0; i < nn; ++i) st.levels[st.nodes[i].height].push_back(i);
+  for (int hgt = 0; hgt <= H; ++hgt) {
+    st.fstart.push_back((int)st.fblocks.size() / 2);
+    st.bstart.push_back((int)st.bblocks.size() / 2);
+    for (int id : st.levels[hgt]) {
+      const SppNode& nd = st.nodes[id];
+      for (int r0 = 0; r0 < nd.ns + nd.nb; r0 += SppStructure::RB) { st.fblocks.push_back(id); st.fblocks.push_back(r0); }
+      for (int r0 = 0; r0 < nd.ns; r0 += SppStructure::RB) { st.bblocks.push_back(id); st.bblocks.push_back(r0); }
+    }
+    st.fcount.push_back((int)st.fblocks.size() / 2 - st.fstart.back());
+    st.bcount.push_back((int)st.bblocks.size() / 2 - st.bstart.back());
+    int fk = 0, bk = 0;
+    for (int id : st.levels[hgt]) {
+      fk = std::max(fk, st.nodes[id].ns);
+      bk = std::max(bk, st.nodes[id].ns + st.nodes[id].nb);
+    }
+    st.fkmax.push_back(fk);
+    st.bkmax.push_back(bk);
+  }
   // contributions: row r receives u[uoff_D + pos] for every node D with bnd_D[pos] = r
   std::vector<std::vector<int>> rows(st.n);
   for (int i = 0; i < nn; ++i) {
@@ -432,16 +449,44 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
         for (int j = k + 1; j < nf; ++j) ri[j] -= l * rk[j];
       }
     }
-    // store blocks; the diagonal of U_SS is stored inverted
-    cd* fss = &out.factor[nd.fss];
-    cd* fbs = &out.factor[nd.fbs];
-    cd* fsb = &out.factor[nd.fsb];
+    // W_f = [L_SS^-1 ; L_BS L_SS^-1], W_b = [U_SS^-1 , -U_SS^-1 U_SB]: with these, each
+    // supernode's forward and backward step is one dense product on the device
+    std::vector<cd> Li((size_t)ns * ns, cd(0.0, 0.0)), Ui((size_t)ns * ns, cd(0.0, 0.0));
+    for (int c = 0; c < ns; ++c) {           // L Li = I, L unit lower (multipliers in F)
+      Li[(size_t)c * ns + c] = 1.0;
+      for (int i = c + 1; i < ns; ++i) {
+        cd acc(0.0, 0.0);
+        for (int k = c; k < i; ++k) acc += F[(size_t)i * nf + k] * Li[(size_t)k * ns + c];
+        Li[(size_t)i * ns + c] = -acc;
+      }
+    }
+    for (int c = ns - 1; c >= 0; --c) {      // U Ui = I, U upper (diagonal = pivots)
+      Ui[(size_t)c * ns + c] = 1.0 / F[(size_t)c * nf + c];
+      for (int i = c - 1; i >= 0; --i) {
+        cd acc(0.0, 0.0);
+        for (int k = i + 1; k <= c; ++k) acc += F[(size_t)i * nf + k] * Ui[(size_t)k * ns + c];
+        Ui[(size_t)i * ns + c] = -acc / F[(size_t)i * nf + i];
+      }
+    }
+    cd* wf = &out.factor[nd.wf];
+    cd* wb = &out.factor[nd.wb];
     for (int i = 0; i < ns; ++i)
-      for (int j = 0; j < ns; ++j) fss[(size_t)i * ns + j] = (i == j) ? 1.0 / F[(size_t)i * nf + j] : F[(size_t)i * nf + j];
+      for (int j = 0; j < ns; ++j) wf[(size_t)i * ns + j] = Li[(size_t)i * ns + j];
     for (int i = 0; i < nb; ++i)
-      for (int j = 0; j < ns; ++j) fbs[(size_t)i * ns + j] = F[(size_t)(ns + i) * nf + j];
-    for (int i = 0; i < ns; ++i)
-      for (int j = 0; j < nb; ++j) fsb[(size_t)i * nb + j] = F[(size_t)i * nf + ns + j];
+      for (int j = 0; j < ns; ++j) {
+        cd acc(0.0, 0.0);
+        for (int k = j; k < ns; ++k) acc += F[(size_t)(ns + i) * nf + k] * Li[(size_t)k * ns + j];
+        wf[(size_t)(ns + i) * ns + j] = acc;
+      }
+    const int kb = ns + nb;
+    for (int i = 0; i < ns; ++i) {
+      for (int j = 0; j < ns; ++j) wb[(size_t)i * kb + j] = Ui[(size_t)i * ns + j];
+      for (int j = 0; j < nb; ++j) {
+        cd acc(0.0, 0.0);
+        for (int k = i; k < ns; ++k) acc += Ui[(size_t)i * ns + k] * F[(size_t)k * nf + ns + j];
+        wb[(size_t)i * kb + ns + j] = -acc;
+      }
+    }
     upd[s].resize((size_t)nb * nb);
     for (int i = 0; i < nb; ++i)
       for (int j = 0; j < nb; ++j) upd[s][(size_t)i * nb + j] = F[(size_t)(ns + i) * nf + ns + j];

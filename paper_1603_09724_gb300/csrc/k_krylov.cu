@@ -117,76 +117,84 @@ cudaError_t launch_krylov_restart(bool dbl, KrylovDims d, const void* b, const v
 }
 
 // ------------------------------------------------------------------ CGS2
-template <typename T>
-__global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, int k, cx_t<T>* __restrict__ V,
+// Classical Gram-Schmidt with one re-orthogonalisation of w against V_0..V_{KK-1}
+// (KK = k + 1 is a template parameter so that the per-thread partial sums and basis
+// values stay in registers).  Three sweeps over the basis:
+//   1: h1 = V^H w
+//   2: w' = w - V h1 (on the fly), h2 = V^H w', |w'|^2
+//   3: w'' = w - V (h1 + h2), written as V_{k+1} = w'' / |w''| with
+//      |w''|^2 = |w'|^2 - |h2|^2 (w'' is orthogonal to V, which is orthonormal).
+template <typename T, int KK>
+__global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, cx_t<T>* __restrict__ V,
                                                          const cx_t<T>* __restrict__ w, double2* __restrict__ H,
                                                          const int* __restrict__ active) {
   using C = cx_t<T>;
-  __shared__ double sh[2 * KMAX * (KT / 32)];
+  constexpr int k = KK - 1;
+  __shared__ double sh[(2 * KK + 1) * (KT / 32)];
   const int s = blockIdx.x;
   if (!active[s]) return;
   const size_t n = d.n;
   const size_t vs = (size_t)d.S * n;   // stride between basis vectors
   const C* ws = w + (size_t)s * n;
   const C* Vs = V + (size_t)s * n;
-  double h[2 * KMAX];
-  double h1[2 * KMAX];
-  C ht[KMAX];
-  // pass 1: h1 = V^H w (per-thread partials in the working precision, FP64 across threads)
+  double h[2 * KK + 1];
+  C ht[KK];
+  C h1c[KK];
+  // sweep 1
 #pragma unroll
-  for (int q = 0; q < KMAX; ++q) ht[q] = mk<C>(0, 0);
+  for (int q = 0; q < KK; ++q) ht[q] = mk<C>(0, 0);
   for (size_t i = threadIdx.x; i < n; i += KT) {
     const C wi = ws[i];
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j <= k) ht[j] = cfmac(Vs[j * vs + i], wi, ht[j]);
+    for (int j = 0; j < KK; ++j) ht[j] = cfmac(Vs[j * vs + i], wi, ht[j]);
   }
 #pragma unroll
-  for (int q = 0; q < KMAX; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
-  block_reduce<2 * KMAX>(h, sh);
+  for (int q = 0; q < KK; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
+  h[2 * KK] = 0.0;
+  block_reduce<2 * KK + 1>(h, sh);
+  double h1[2 * KK];
 #pragma unroll
-  for (int q = 0; q < 2 * KMAX; ++q) h1[q] = h[q];
-  // pass 2: h2 = V^H (w - V h1)
+  for (int q = 0; q < 2 * KK; ++q) h1[q] = h[q];
 #pragma unroll
-  for (int q = 0; q < KMAX; ++q) ht[q] = mk<C>(0, 0);
+  for (int j = 0; j < KK; ++j) h1c[j] = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
+  // sweep 2
+#pragma unroll
+  for (int q = 0; q < KK; ++q) ht[q] = mk<C>(0, 0);
+  T nw = 0;
   for (size_t i = threadIdx.x; i < n; i += KT) {
     C wi = ws[i];
-    C vv[KMAX];
+    C vv[KK];
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j <= k) {
-        vv[j] = Vs[j * vs + i];
-        const C hj = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
-        wi = csub(wi, cmul(hj, vv[j]));
-      }
+    for (int j = 0; j < KK; ++j) {
+      vv[j] = Vs[j * vs + i];
+      wi = csub(wi, cmul(h1c[j], vv[j]));
+    }
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j <= k) ht[j] = cfmac(vv[j], wi, ht[j]);
+    for (int j = 0; j < KK; ++j) ht[j] = cfmac(vv[j], wi, ht[j]);
+    nw += wi.x * wi.x + wi.y * wi.y;
   }
 #pragma unroll
-  for (int q = 0; q < KMAX; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
-  block_reduce<2 * KMAX>(h, sh);
+  for (int q = 0; q < KK; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
+  h[2 * KK] = (double)nw;
+  block_reduce<2 * KK + 1>(h, sh);
+  double h2sq = 0.0;
 #pragma unroll
-  for (int q = 0; q < 2 * KMAX; ++q) h1[q] += h[q];
-  // pass 3: w'' = w - V (h1 + h2), norm, store into V_{k+1}
-  C* vk1 = V + (size_t)(k + 1) * vs + (size_t)s * n;
-  T nt = 0;
-  for (size_t i = threadIdx.x; i < n; i += KT) {
-    C wi = ws[i];
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j <= k) {
-        const C hj = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
-        wi = csub(wi, cmul(hj, Vs[j * vs + i]));
-      }
-    nt += wi.x * wi.x + wi.y * wi.y;
-    vk1[i] = wi;
+  for (int q = 0; q < 2 * KK; ++q) {
+    h2sq += h[q] * h[q];
+    h1[q] += h[q];
   }
-  double nr[1] = {(double)nt};
-  block_reduce<1>(nr, sh);
-  const double hn = sqrt(nr[0]);
+  const double hn = sqrt(fmax(h[2 * KK] - h2sq, 0.0));
   const T inv = hn > 0.0 ? (T)(1.0 / hn) : T(0);
-  for (size_t i = threadIdx.x; i < n; i += KT) vk1[i] = cscale(vk1[i], inv);
+#pragma unroll
+  for (int j = 0; j < KK; ++j) h1c[j] = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
+  // sweep 3
+  C* vk1 = V + (size_t)(k + 1) * vs + (size_t)s * n;
+  for (size_t i = threadIdx.x; i < n; i += KT) {
+    C wi = ws[i];
+#pragma unroll
+    for (int j = 0; j < KK; ++j) wi = csub(wi, cmul(h1c[j], Vs[j * vs + i]));
+    vk1[i] = cscale(wi, inv);
+  }
   if (threadIdx.x == 0) {
     double2* Hs = H + (size_t)s * (KMAX + 1) * KMAX;
     for (int j = 0; j <= k; ++j) Hs[j * KMAX + k] = make_double2(h1[2 * j], h1[2 * j + 1]);
@@ -194,14 +202,27 @@ __global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, int k, cx
   }
 }
 
+template <typename T>
+static cudaError_t orth_dispatch(KrylovDims d, int k, void* V, void* w, double2* H, const int* active,
+                                 cudaStream_t st) {
+  using C = cx_t<T>;
+#define ORTH_CASE(KK_)                                                                                   \
+  case KK_:                                                                                              \
+    krylov_orth_kernel<T, KK_><<<d.S, KT, 0, st>>>(d, (C*)V, (const C*)w, H, active);                    \
+    break;
+  switch (k + 1) {
+    ORTH_CASE(1) ORTH_CASE(2) ORTH_CASE(3) ORTH_CASE(4) ORTH_CASE(5) ORTH_CASE(6) ORTH_CASE(7) ORTH_CASE(8)
+    ORTH_CASE(9) ORTH_CASE(10) ORTH_CASE(11) ORTH_CASE(12) ORTH_CASE(13) ORTH_CASE(14) ORTH_CASE(15)
+    default: return cudaErrorInvalidValue;
+  }
+#undef ORTH_CASE
+  return cudaGetLastError();
+}
+
 cudaError_t launch_krylov_orth(bool dbl, KrylovDims d, int k, void* V, void* w, double2* H, const int* active,
                                cudaStream_t st) {
-  if (k + 1 >= KMAX + 1) return cudaErrorInvalidValue;
-  if (dbl)
-    krylov_orth_kernel<double><<<d.S, KT, 0, st>>>(d, k, (double2*)V, (const double2*)w, H, active);
-  else
-    krylov_orth_kernel<float><<<d.S, KT, 0, st>>>(d, k, (float2*)V, (const float2*)w, H, active);
-  return cudaGetLastError();
+  if (k < 0 || k + 1 > 15) return cudaErrorInvalidValue;
+  return dbl ? orth_dispatch<double>(d, k, V, w, H, active, st) : orth_dispatch<float>(d, k, V, w, H, active, st);
 }
 
 // ------------------------------------------------------------------ Givens

@@ -1,18 +1,17 @@
 // Device triangular solves with the multifrontal factor of the sparsifying matrix P
 // (Sec. 3.2: u~ = P^-1 Q G b, "solved by sparse direct solvers such as nested
-// dissection").  Unknowns are numbered in nested-dissection postorder; each supernode s
-// owns a contiguous range [off, off + ns) and a boundary list B(s) of ancestor unknowns.
+// dissection").  Unknowns are numbered in nested-dissection postorder; supernode s owns
+// the contiguous range [off, off + ns) and couples to the ancestor unknowns B(s).
 //
-// Forward (L y = b), leaves first, one launch per tree height:
-//   y_S = b_S - sum of the update rows u_D that target S (deterministic gather)
-//   y_S = L_SS^-1 y_S   (unit lower, column sweep with one barrier per column)
-//   u_s = L_BS y_S      (update rows for the ancestors)
-// Backward (U x = y), root first:
-//   t = y_S - U_SB x_B  (x_B gathered from the ancestors' finished unknowns)
-//   x_S = U_SS^-1 t     (upper, the diagonal stored inverted)
-// A CTA handles one supernode of one pole for RT right-hand sides; b and x are in the
-// natural grid order (gathered / scattered through the ND permutation), y is kept in ND
-// order.  System s = p * N + c uses pole p's factor.
+// With W_f = [L_SS^-1 ; L_BS L_SS^-1] and W_b = [U_SS^-1 , -U_SS^-1 U_SB] (built on the
+// host) every supernode step is one dense complex product over a tile of right-hand
+// sides, with no sequential sweep:
+//   forward  (leaves first):  [y_S ; u_s] = W_f (b_S - sum of the update rows u_D that
+//            target S)            -- y_S kept in ND order, u_s for the ancestors
+//   backward (root first):    x_S = W_b [y_S ; x_B]   -- x_B gathered from the ancestors
+// One launch per tree height and direction.  A CTA computes RB = 64 rows of one
+// supernode's product for RT right-hand sides of one pole (system s = p * N + c), with
+// the right-hand-side block staged in shared memory and 4 x (RT/8) outputs per thread.
 #include "common.cuh"
 #include "trsv.h"
 
@@ -22,163 +21,166 @@ template <typename T> struct TrsvCfg;
 template <> struct TrsvCfg<float> { static constexpr int RT = 32; };
 template <> struct TrsvCfg<double> { static constexpr int RT = 16; };
 constexpr int TS_THREADS = 128;
+constexpr int RB = 64;   // rows per CTA
+constexpr int KT = 16;   // k step of the product
 
-template <typename T>
-__global__ void __launch_bounds__(TS_THREADS) lsolve_kernel(TrsvArgs a, const int* __restrict__ level_nodes,
-                                                            const cx_t<T>* __restrict__ b, cx_t<T>* __restrict__ ynd,
-                                                            cx_t<T>* __restrict__ u, const cx_t<T>* __restrict__ factor,
-                                                            const int* __restrict__ active) {
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks,
+                                                               const cx_t<T>* __restrict__ b, cx_t<T>* __restrict__ ynd,
+                                                               cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
+                                                               const cx_t<T>* __restrict__ factor,
+                                                               const int* __restrict__ active) {
   using C = cx_t<T>;
   constexpr int RT = TrsvCfg<T>::RT;
+  constexpr int TC = RT / 8;   // columns per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* y = reinterpret_cast<C*>(smem_raw);   // [ns][RT]
-  const int node = level_nodes[blockIdx.x];
+  C* Bs = reinterpret_cast<C*>(smem_raw);   // [K][RT]
+  __shared__ C As[KT][RB + 1];
+  __shared__ C Cs[RB][RT + 1];
+  const int node = blocks[2 * blockIdx.x], r0 = blocks[2 * blockIdx.x + 1];
   const int p = blockIdx.y;
   const int c0 = blockIdx.z * RT;
-  const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node], uoff = a.node_uoff[node];
-  const C* f = factor + (size_t)p * a.factor_size;
-  const C* Lss = f + a.node_fss[node];
-  const C* Lbs = f + a.node_fbs[node];
+  const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
+  const int K = FWD ? ns : ns + nb;
+  const int M = FWD ? ns + nb : ns;
+  const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
-  // load b (natural order, gathered); i fastest for coalescing
-  for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {
-    const int i = idx % ns, cc = idx / ns;
-    const int c = c0 + cc;
-    C v = mk<C>(0, 0);
-    if (c < a.N) {
+  // ---- right-hand-side block
+  if (FWD) {
+    for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {   // i fastest: coalesced along a line
+      const int i = idx % ns, cc = idx / ns;
+      const int c = c0 + cc;
+      C v = mk<C>(0, 0);
+      if (c < a.N) {
+        const size_t s = (size_t)p * a.N + c;
+        if (!active || active[s]) v = b[s * a.n + a.perm[off + i]];
+      }
+      Bs[i * RT + cc] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {   // cc fastest: u rows are [row][system]
+      const int cc = idx % RT, i = idx / RT;
+      const int c = c0 + cc;
+      if (c >= a.N) continue;
       const size_t s = (size_t)p * a.N + c;
-      if (!active || active[s]) v = b[s * a.n + a.perm[off + i]];
+      const int e0 = a.contrib_ptr[off + i], e1 = a.contrib_ptr[off + i + 1];
+      if (e0 == e1) continue;
+      C acc = Bs[i * RT + cc];
+      for (int e = e0; e < e1; ++e) acc = csub(acc, u[(size_t)a.contrib_idx[e] * a.S + s]);
+      Bs[i * RT + cc] = acc;
     }
-    y[i * RT + cc] = v;
+  } else {
+    const int boff = a.node_boff[node];
+    for (int idx = tid; idx < K * RT; idx += TS_THREADS) {
+      const int i = idx % K, cc = idx / K;
+      const int c = c0 + cc;
+      C v = mk<C>(0, 0);
+      if (c < a.N) {
+        const size_t s = (size_t)p * a.N + c;
+        v = (i < ns) ? ynd[s * a.n + off + i] : x[s * a.n + a.bnat[boff + i - ns]];
+      }
+      Bs[i * RT + cc] = v;
+    }
   }
   __syncthreads();
-  // subtract the descendants' update rows (cc fastest: u rows are [row][system])
-  for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {
-    const int cc = idx % RT, i = idx / RT;
-    const int c = c0 + cc;
-    if (c >= a.N) continue;
-    const size_t s = (size_t)p * a.N + c;
-    C acc = y[i * RT + cc];
-    const int e0 = a.contrib_ptr[off + i], e1 = a.contrib_ptr[off + i + 1];
-    for (int e = e0; e < e1; ++e) acc = csub(acc, u[(size_t)a.contrib_idx[e] * a.S + s]);
-    y[i * RT + cc] = acc;
+  // ---- product: rows r0 .. r0 + RB - 1 of W times Bs
+  const int tr = tid / 8, tcg = tid % 8;   // 16 row groups x 8 column groups
+  C acc[4][TC];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TC; ++j) acc[i][j] = mk<C>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += KT) {
+    for (int idx = tid; idx < RB * KT; idx += TS_THREADS) {   // k fastest: coalesced rows of W
+      const int kk = idx % KT, rr = idx / KT;
+      const int r = r0 + rr, k = k0 + kk;
+      As[kk][rr] = (r < M && k < K) ? W[(size_t)r * K + k] : mk<C>(0, 0);
+    }
+    __syncthreads();
+    const int kmax = min(KT, K - k0);
+    for (int kk = 0; kk < kmax; ++kk) {
+      C av[4], bv[TC];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][tr * 4 + i];
+#pragma unroll
+      for (int j = 0; j < TC; ++j) bv[j] = Bs[(k0 + kk) * RT + tcg * TC + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TC; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TC; ++j) Cs[tr * 4 + i][tcg * TC + j] = acc[i][j];
   __syncthreads();
-  // unit lower triangular solve
-  for (int k = 0; k < ns - 1; ++k) {
-    const int rows = ns - k - 1;
+  const int rows = min(RB, M - r0);
+  if (FWD) {
+    // y rows (ND order, rr fastest) and update rows (system fastest)
+    const int ny = max(0, min(rows, ns - r0));
+    for (int idx = tid; idx < ny * RT; idx += TS_THREADS) {
+      const int rr = idx % ny, cc = idx / ny;
+      const int c = c0 + cc;
+      if (c < a.N) ynd[((size_t)p * a.N + c) * a.n + off + r0 + rr] = Cs[rr][cc];
+    }
+    const int uoff = a.node_uoff[node];
+    for (int idx = tid; idx < (rows - ny) * RT; idx += TS_THREADS) {
+      const int cc = idx % RT, rr = ny + idx / RT;
+      const int c = c0 + cc;
+      if (c < a.N) u[(size_t)(uoff + r0 + rr - ns) * a.S + (size_t)p * a.N + c] = Cs[rr][cc];
+    }
+  } else {
     for (int idx = tid; idx < rows * RT; idx += TS_THREADS) {
-      const int cc = idx % RT, i = k + 1 + idx / RT;
-      y[i * RT + cc] = csub(y[i * RT + cc], cmul(Lss[(size_t)i * ns + k], y[k * RT + cc]));
+      const int rr = idx % rows, cc = idx / rows;
+      const int c = c0 + cc;
+      if (c >= a.N) continue;
+      const size_t s = (size_t)p * a.N + c;
+      if (active && !active[s]) continue;
+      x[s * a.n + a.perm[off + r0 + rr]] = Cs[rr][cc];
     }
-    __syncthreads();
-  }
-  // store y (ND order)
-  for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {
-    const int i = idx % ns, cc = idx / ns;
-    const int c = c0 + cc;
-    if (c < a.N) ynd[((size_t)p * a.N + c) * a.n + off + i] = y[i * RT + cc];
-  }
-  // update rows u = L_BS y
-  for (int idx = tid; idx < nb * RT; idx += TS_THREADS) {
-    const int cc = idx % RT, j = idx / RT;
-    const int c = c0 + cc;
-    if (c >= a.N) continue;
-    const C* lr = Lbs + (size_t)j * ns;
-    C acc = mk<C>(0, 0);
-    for (int i = 0; i < ns; ++i) acc = cfma(lr[i], y[i * RT + cc], acc);
-    u[(size_t)(uoff + j) * a.S + (size_t)p * a.N + c] = acc;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(TS_THREADS) usolve_kernel(TrsvArgs a, const int* __restrict__ level_nodes,
-                                                            const cx_t<T>* __restrict__ ynd, cx_t<T>* __restrict__ x,
-                                                            const cx_t<T>* __restrict__ factor,
-                                                            const int* __restrict__ active) {
-  using C = cx_t<T>;
-  constexpr int RT = TrsvCfg<T>::RT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int node = level_nodes[blockIdx.x];
-  const int p = blockIdx.y;
-  const int c0 = blockIdx.z * RT;
-  const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node], boff = a.node_boff[node];
-  C* y = reinterpret_cast<C*>(smem_raw);   // [ns][RT]
-  C* xb = y + (size_t)ns * RT;             // [nb][RT]
-  const C* f = factor + (size_t)p * a.factor_size;
-  const C* Uss = f + a.node_fss[node];
-  const C* Usb = f + a.node_fsb[node];
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {
-    const int i = idx % ns, cc = idx / ns;
-    const int c = c0 + cc;
-    y[i * RT + cc] = (c < a.N) ? ynd[((size_t)p * a.N + c) * a.n + off + i] : mk<C>(0, 0);
-  }
-  for (int idx = tid; idx < nb * RT; idx += TS_THREADS) {
-    const int j = idx % nb, cc = idx / nb;
-    const int c = c0 + cc;
-    xb[j * RT + cc] = (c < a.N) ? x[((size_t)p * a.N + c) * a.n + a.bnat[boff + j]] : mk<C>(0, 0);
-  }
-  __syncthreads();
-  if (nb > 0) {
-    for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {
-      const int cc = idx % RT, i = idx / RT;
-      const C* ur = Usb + (size_t)i * nb;
-      C acc = y[i * RT + cc];
-      for (int j = 0; j < nb; ++j) acc = csub(acc, cmul(ur[j], xb[j * RT + cc]));
-      y[i * RT + cc] = acc;
-    }
-    __syncthreads();
-  }
-  // upper solve: at step k, x_k = d_k y_k is final; rows i < k subtract U_ik x_k
-  for (int k = ns - 1; k > 0; --k) {
-    const C dk = Uss[(size_t)k * ns + k];
-    for (int idx = tid; idx < k * RT; idx += TS_THREADS) {
-      const int cc = idx % RT, i = idx / RT;
-      const C xk = cmul(dk, y[k * RT + cc]);
-      y[i * RT + cc] = csub(y[i * RT + cc], cmul(Uss[(size_t)i * ns + k], xk));
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {
-    const int i = idx % ns, cc = idx / ns;
-    const int c = c0 + cc;
-    if (c >= a.N) continue;
-    const size_t s = (size_t)p * a.N + c;
-    if (active && !active[s]) continue;
-    x[s * a.n + a.perm[off + i]] = cmul(Uss[(size_t)i * ns + i], y[i * RT + cc]);
   }
 }
 
 size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb) {
   const int RT = dbl ? TrsvCfg<double>::RT : TrsvCfg<float>::RT;
   const size_t cs = dbl ? sizeof(double2) : sizeof(float2);
-  return (size_t)(max_ns + max_nb) * RT * cs;
+  const size_t stat = cs * ((size_t)KT * (RB + 1) + (size_t)RB * (RT + 1));
+  return (size_t)(max_ns + max_nb) * RT * cs + stat;   // dynamic part is the first term
 }
 
 template <typename T>
 static cudaError_t run_t(const TrsvArgs& a, const TrsvLevels& lv, int P, const void* b, void* ynd, void* u, void* x,
-                         const void* factor, const int* active, size_t smem, cudaStream_t st) {
+                         const void* factor, const int* active, size_t smem_total, cudaStream_t st) {
+  using C = cx_t<T>;
   constexpr int RT = TrsvCfg<T>::RT;
+  const size_t stat = sizeof(C) * ((size_t)KT * (RB + 1) + (size_t)RB * (RT + 1));
+  const size_t dyn = smem_total - stat;
   // the opt-in shared-memory limit only ever grows (handles of different grids share the kernels)
   static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(lsolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (dyn > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(trsv_gemm_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(usolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(trsv_gemm_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
+    attr_bytes = dyn;
   }
   const int tiles = (a.N + RT - 1) / RT;
+  // dynamic shared memory sized per level (the leaves need a few KB, the root fronts ~100 KB)
   for (int h = 0; h < lv.nlevels; ++h) {
-    dim3 grid(lv.count[h], P, tiles);
-    lsolve_kernel<T><<<grid, TS_THREADS, smem, st>>>(a, lv.nodes + lv.start[h], (const cx_t<T>*)b, (cx_t<T>*)ynd,
-                                                     (cx_t<T>*)u, (const cx_t<T>*)factor, active);
+    if (lv.fcount[h] == 0) continue;
+    dim3 grid(lv.fcount[h], P, tiles);
+    const size_t sm = (size_t)lv.fkmax[h] * RT * sizeof(C);
+    trsv_gemm_kernel<T, true><<<grid, TS_THREADS, sm, st>>>(a, lv.fblocks + 2 * lv.fstart[h], (const C*)b, (C*)ynd,
+                                                            (C*)u, (C*)x, (const C*)factor, active);
   }
   for (int h = lv.nlevels - 1; h >= 0; --h) {
-    dim3 grid(lv.count[h], P, tiles);
-    usolve_kernel<T><<<grid, TS_THREADS, smem, st>>>(a, lv.nodes + lv.start[h], (const cx_t<T>*)ynd, (cx_t<T>*)x,
-                                                     (const cx_t<T>*)factor, active);
+    if (lv.bcount[h] == 0) continue;
+    dim3 grid(lv.bcount[h], P, tiles);
+    const size_t sm = (size_t)lv.bkmax[h] * RT * sizeof(C);
+    trsv_gemm_kernel<T, false><<<grid, TS_THREADS, sm, st>>>(a, lv.bblocks + 2 * lv.bstart[h], (const C*)b, (C*)ynd,
+                                                             (C*)u, (C*)x, (const C*)factor, active);
   }
   return cudaGetLastError();
 }

@@ -17,7 +17,8 @@ struct SppNode {
   int nb;       // boundary size |B(s)| (ancestor unknowns coupled to the subtree)
   int boff;     // offset into SppStructure::bnat / bnd
   int uoff;     // first row of this node's update vector in the u buffer
-  long long fss, fbs, fsb;   // offsets of the dense blocks in a pole's factor array
+  long long wf;  // offset of W_f = [L_SS^-1 ; L_BS L_SS^-1] ((ns + nb) x ns, row-major) in a pole's factor
+  long long wb;  // offset of W_b = [U_SS^-1 , -U_SS^-1 U_SB] (ns x (ns + nb), row-major)
   int parent;   // parent node (-1 at the root)
   int height;   // 0 for leaves
 };
@@ -37,12 +38,16 @@ struct SppStructure {
   long long factor_size = 0;   // complex entries per pole
   int max_ns = 0, max_nb = 0;
   std::vector<int> offsets;    // stencil offsets, flattened (dx, dy, dz) triples, x fastest
+  // row blocks of RB rows per level for the device products: (node, first row) pairs
+  static constexpr int RB = 64;
+  std::vector<int> fblocks, bblocks;
+  std::vector<int> fstart, fcount, bstart, bcount;
+  std::vector<int> fkmax, bkmax;   // per level: largest K of the forward / backward products
 };
 
 struct SppPole {
   std::vector<cd> q;            // stencil row (|a| entries, same order as offsets)
-  std::vector<cd> factor;       // dense blocks, per node: L\U of S (ns x ns, row-major),
-                                // L_BS (nb x ns row-major), U_SB (ns x nb row-major)
+  std::vector<cd> factor;       // per node W_f and W_b (see SppNode)
   double pivot_min = 0, pivot_max = 0;
   int nperturbed = 0;
   double sigma_min = 0, sigma_max = 0;   // singular values of G(a, a^c)

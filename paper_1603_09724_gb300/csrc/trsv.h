@@ -13,23 +13,24 @@ struct TrsvArgs {
   const int* node_off;
   const int* node_boff;
   const int* node_uoff;
-  const long long* node_fss;
-  const long long* node_fbs;
-  const long long* node_fsb;
-  const int* perm;          // ND -> natural
-  const int* bnat;          // boundary natural indices
-  const int* contrib_ptr;   // n + 1
+  const long long* node_wf;   // W_f offset ((ns + nb) x ns, row-major)
+  const long long* node_wb;   // W_b offset (ns x (ns + nb), row-major)
+  const int* perm;            // ND -> natural
+  const int* bnat;            // boundary natural indices
+  const int* contrib_ptr;     // n + 1
   const int* contrib_idx;
-  long long factor_size;    // complex entries per pole
-  size_t n;                 // grid points
-  int N;                    // right-hand sides per pole
-  size_t S;                 // total systems (rows stride of the u buffer)
+  long long factor_size;      // complex entries per pole
+  size_t n;                   // grid points
+  int N;                      // right-hand sides per pole
+  size_t S;                   // total systems (rows stride of the u buffer)
 };
 
 struct TrsvLevels {
   int nlevels;
-  const int* nodes;               // device: node ids grouped by height
-  std::vector<int> start, count;  // host
+  const int* fblocks;         // device: (node, first row) pairs, forward products, by height
+  const int* bblocks;         // device: same for the backward products
+  std::vector<int> fstart, fcount, bstart, bcount;   // host, per height
+  std::vector<int> fkmax, bkmax;                      // host, per height: shared-memory sizing
 };
 
 size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb);

@@ -190,6 +190,25 @@ omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
  * number of perturbed pivots. */
 omm_status omm_factor_info(omm_t h, int pole, int* nsuper, long long* nnz, double* pivot_ratio, int* nperturbed);
 
+/* C = A^* B like omm_gram, but without a handle and without allocating any device
+ * memory (the paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc, e.g. code that runs inside another framework's memory manager which has
+ * already reserved the device memory, or paths where the implicit synchronisation and
+ * latency of cudaMalloc/cudaFree are not acceptable).
+ * precision: OMM_FP64 (A, B complex128) or OMM_MIXED (complex64); A: n x na and B: n x nb,
+ * device, column-major; C: na x nb complex128, row-major, device; stream: cudaStream_t.
+ * The split-K partial sums live in a fixed 8 MiB device array compiled into the library
+ * (524288 complex128 entries, held by every GPU that loads the library until the process
+ * exits).  na * nb must not exceed 524288, else OMM_EINVAL (the message says why).
+ * The first call on a device, with that device current, resolves the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's partials (every partial is
+ * written before it is read, so nothing needs clearing): calls that overlap on the GPU
+ * (different streams, or different host threads on one device) race and must be
+ * serialised by the caller.  Asynchronous with respect to the host. */
+omm_status omm_gram_noalloc(int precision, const void* A, int na, const void* B, int nb, size_t n, void* C,
+                            void* stream);
+
 /* Device allocator hook used by subsequent omm_create calls (NULL, NULL restores
  * cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or NULL. */
 omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx);

@@ -75,6 +75,7 @@ _SIGS = {
     "omm_profile_enable": (C.c_int, [_vp, C.c_int]),
     "omm_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _dp, _dp]),
     "omm_profile_class_name": (C.c_char_p, [C.c_int]),
+    "omm_gram_noalloc": (C.c_int, [C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_size_t, _vp, _vp]),
 }
 PROFILE_CLASSES = ("happly", "greenq", "trsv", "orth", "gram", "block_update", "vector", "small")
 for _name, (_res, _args) in _SIGS.items():

@@ -288,3 +288,76 @@ cudaError_t launch_convert(bool to_dbl, size_t count, const void* src, void* dst
 }
 
 }  // namespace omm
+
+// ------------------------------------------------------------------ Gram without device allocation
+// omm_gram_noalloc: the split-K Gram above with its partial sums kept in a fixed device
+// array instead of a work buffer, for callers that cannot call cudaMalloc.  The array is
+// a file-scope __device__ variable: every GPU that loads the library holds it until the
+// process exits, and every call on a device shares it.
+#include <mutex>
+
+namespace omm {
+namespace {
+constexpr size_t kNoAllocPartials = (size_t)1 << 19;   // double2 entries (8 MiB per device)
+__device__ __align__(256) double2 g_noalloc_partials[kNoAllocPartials];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+}  // namespace omm
+
+extern "C" omm_status omm_gram_noalloc(int precision, const void* A, int na, const void* B, int nb, size_t n, void* C,
+                                       void* stream) {
+  using namespace omm;
+  if ((precision != OMM_FP64 && precision != OMM_MIXED) || !A || !B || !C || na < 1 || nb < 1 || n < 1)
+    return OMM_EINVAL;
+  if ((size_t)na * nb > kNoAllocPartials) {
+    omm_internal_set_cuda_error(cudaErrorInvalidValue, "omm_gram_noalloc: na * nb exceeds the static capacity of 524288 entries",
+                                __FILE__, __LINE__);
+    return OMM_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    omm_internal_set_cuda_error(e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice", __FILE__, __LINE__);
+    return OMM_ECUDA;
+  }
+  double2* part = nullptr;
+  {
+    // set-up, once per device with that device current: the host-side name of the array
+    // is not a device address, so resolve it
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+      if (e != cudaSuccess) {
+        omm_internal_set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_partials)", __FILE__, __LINE__);
+        return OMM_ECUDA;
+      }
+      g_noalloc_ptr[dev] = (double2*)p;
+    }
+    part = g_noalloc_ptr[dev];
+  }
+  // split K so that the partials fit the fixed array (each partial is written before it is read)
+  int ks = gram_splits(na, nb, n);
+  const int fit = (int)(kNoAllocPartials / ((size_t)na * nb));
+  if (ks > fit) ks = fit;
+  size_t kchunk = (n + ks - 1) / ks;
+  kchunk = (kchunk + GK - 1) / GK * GK;
+  ks = (int)((n + kchunk - 1) / kchunk);
+  cudaStream_t st = (cudaStream_t)stream;
+  dim3 grid((na + GT - 1) / GT, (nb + GT - 1) / GT, ks);
+  if (precision == OMM_FP64)
+    gram_partial_kernel<double><<<grid, 256, 0, st>>>((const double2*)A, na, (const double2*)B, nb, n, kchunk, part);
+  else
+    gram_partial_kernel<float><<<grid, 256, 0, st>>>((const float2*)A, na, (const float2*)B, nb, n, kchunk, part);
+  const int tot = na * nb;
+  gram_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(part, ks, na, nb, (double2*)C, nb);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    omm_internal_set_cuda_error(e, "omm_gram_noalloc launch", __FILE__, __LINE__);
+    return OMM_ECUDA;
+  }
+  return OMM_OK;
+}

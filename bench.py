@@ -182,6 +182,20 @@ def run_reference(a):
     print(json.dumps(rec))
 
 
+# ------------------------------------------------------------------------------ replicas
+def aggregate_ranks(ms_local, steps, world, device="cpu"):
+    """Whole-job throughput of independent replicas: the slowest rank's timed region
+    (MAX over ranks) and value = world * steps / that time (solves/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1000.0)
+
+
 # ------------------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import numpy as np
@@ -249,12 +263,7 @@ def run_ours(a):
         s.profile(False)
     clk = clocks.stop()
     lat_ms = sorted(x.elapsed_time(y) for x, y in lat)
-    tmax = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    ms_max = float(tmax.item())
-    value = world * a.steps / (ms_max / 1000.0)
+    ms_max, value = aggregate_ranks(ms, a.steps, world, "cuda")
 
     # end to end through the public API with host buffers (pinned), copies in the timed region
     Xout = torch.empty_like(X0h).pin_memory()
@@ -321,8 +330,8 @@ def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w):
     import numpy as np
     try:
         Xm = s.get_orbitals().cpu().numpy().astype(np.complex128)
-        prm =omm.default_params(precision=omm.OMM_FP64, maxit=a.iters if a.iters else 40,
-                                 tol=0.0 if a.iters else 1e-13)
+        prm = omm.default_params(precision=omm.OMM_FP64, maxit=a.iters if a.iters else 40,
+                                 tol=0.0 if a.iters else 1e-13, refilter=a.refilter, gmres_rtol=a.rtol)
         t0 = time.perf_counter()
         s64 = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
         s64.set_poles(z, w)

@@ -81,6 +81,8 @@ typedef struct {
   double tol;           /* CG stop: |E_{m+1} - E_m| <= tol |E_{m+1}| (Sec. 4: 1e-13)   */
   int maxit;            /* maximum CG iterations per round                             */
   int refilter;         /* extra (filter + CG) rounds after the first                  */
+  int gram_tensor;      /* 1: complex64 Grams on tcgen05 tensor cores (TF32 x 3 split,
+                           FP64 split-K sum); 0: CUDA cores.  FP64 handles use CUDA cores */
 } omm_params;
 
 typedef struct {
@@ -89,7 +91,7 @@ typedef struct {
   int converged;           /* 1 if the energy criterion was met                        */
   double energy;           /* E_omm after the last step, from the iteration's Grams    */
   double energy_fp64;      /* E_omm recomputed in FP64 (omm_solve / omm_energy)        */
-  double resid_fp64;       /* ||HX - X S^-1 K||_F / ||HX||_F in FP64 (omm_solve)       */
+  double resid_fp64;       /* ||HX - X S^-1 K||_F / ||X||_F in FP64 (omm_solve)        */
   double gmres_relres_max; /* largest GMRES residual estimate of the last pole solve   */
   int gmres_iters_max;     /* largest GMRES step count of the last pole solve          */
   int gmres_iters_total;   /* sum of GMRES steps over all CG iterations (max per call) */

@@ -99,9 +99,12 @@ struct omm_ctx {
   void* gram64_work = nullptr;
   void* fft_tmp = nullptr;
   size_t fft_tmp_bytes = 0;
+  void* tc_work = nullptr;      // tensor-core Gram split-K partials
+  size_t tc_work_bytes = 0;
+  int* tc_err = nullptr;        // set by the tensor-core Gram if a bounded wait gave up
   void* gw_dbg = nullptr;       // Gram work for omm_gram / the residual check
   size_t gw_dbg_bytes = 0;
-  double2* g2 = nullptr;        // (2N)^2 Gram for the residual check
+  void* m64 = nullptr;          // residual-check N x N matrices and two norms
   int Pfac = 0;                 // poles the factor buffers are sized for
 
   // poles
@@ -148,6 +151,13 @@ struct omm_ctx {
   int* d_cptr = nullptr;
   int* d_cidx = nullptr;
   int* d_fblocks = nullptr;
+  int* d_leaf_nodes = nullptr;
+  long long* d_leaf_voff = nullptr;
+  int* d_leaf_ioff_bs = nullptr;
+  int* d_leaf_ioff_sb = nullptr;
+  int* d_leaf_bs_idx = nullptr;
+  int* d_leaf_sb_idx = nullptr;
+  void* leafvals = nullptr;     // P * leaf_size complex
   int* d_bblocks = nullptr;
   size_t trsv_smem = 0;
   int last_gmres_max = 0;
@@ -408,6 +418,23 @@ TrsvArgs trsv_args(omm_ctx* h, int Ncols, size_t S) {
   return a;
 }
 
+LeafArgs leaf_args(omm_ctx* h, int pole_base) {
+  LeafArgs la;
+  const SppStructure& s = h->spp;
+  la.nleaves = (int)s.leaf_nodes.size();
+  la.bw = s.leaf_bw;
+  for (int id : s.leaf_nodes) la.max_ns = std::max(la.max_ns, s.nodes[id].ns);
+  la.nodes = h->d_leaf_nodes;
+  la.voff = h->d_leaf_voff;
+  la.ioff_bs = h->d_leaf_ioff_bs;
+  la.ioff_sb = h->d_leaf_ioff_sb;
+  la.bs_idx = h->d_leaf_bs_idx;
+  la.sb_idx = h->d_leaf_sb_idx;
+  la.leaf_size = s.leaf_size;
+  la.vals = (const char*)h->leafvals + (size_t)pole_base * s.leaf_size * h->csz;
+  return la;
+}
+
 TrsvLevels trsv_levels(omm_ctx* h) {
   TrsvLevels lv;
   lv.nlevels = (int)h->spp.levels.size();
@@ -437,7 +464,8 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   int nk = 0;
   for (int l = 0; l < lv.nlevels; ++l) nk += (lv.fcount[l] > 0) + (lv.bcount[l] > 0);
   PROF(PC_TRSV, bytes, nk,
-       cuda_status(launch_spp_solve(h->dbl, a, lv, P, tmp, h->ynd, h->ubuf, Z, h->factor, active, h->trsv_smem, h->st),
+       cuda_status(launch_spp_solve(h->dbl, a, lv, leaf_args(h, 0), P, tmp, h->ynd, h->ubuf, Z, h->factor, active,
+                                    h->trsv_smem, h->st),
                    "spp"));
   return OMM_OK;
 }
@@ -524,15 +552,38 @@ omm_status gmres_stats(omm_ctx* h) {
 
 omm_status read_scalars(omm_ctx* h) {
   OMM_TRY(cuda_status(cudaMemcpyAsync(h->sc_h, h->sc, sizeof(OmmScalars), cudaMemcpyDeviceToHost, h->st), "sc"));
+  if (h->tc_err) {
+    int e = 0;
+    OMM_TRY(cuda_status(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st), "tc err"));
+    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sc sync"));
+    if (e) return OMM_ETIMEOUT;
+    return OMM_OK;
+  }
   return cuda_status(cudaStreamSynchronize(h->st), "sc sync");
+}
+
+// C = A^H B (complex double out): tensor cores for complex64 when enabled, else CUDA cores
+omm_status gram_any(omm_ctx* h, const void* A, int na, const void* B, int nb, double2* C, int ldc, void* cc_work) {
+  if (!h->dbl && h->prm.gram_tensor && gram_tc_supported(h->n)) {
+    const size_t need = gram_tc_work_bytes(na, nb, h->n);
+    if (need > h->tc_work_bytes) {
+      OMM_TRY(h->dalloc(&h->tc_work, need));
+      h->tc_work_bytes = need;
+    }
+    if (!h->tc_err) {
+      OMM_TRY(h->dalloc_t(&h->tc_err, sizeof(int)));
+      OMM_TRY(cuda_status(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st), "memset"));
+    }
+    return cuda_status(launch_gram_tc(A, na, B, nb, h->n, C, ldc, h->tc_work, h->tc_err, h->st), "gram_tc");
+  }
+  return cuda_status(launch_gram(h->dbl, A, na, B, nb, h->n, C, ldc, cc_work, h->st), "gram");
 }
 
 // Grams of the current X and the gradient update matrices (t = 0)
 omm_status start_cg(omm_ctx* h) {
   OMM_TRY(happly(h, h->X(), h->HX(), h->N, h->zero_shift, h->N, nullptr));
   PROF(PC_GRAM, 5.0 * h->N * h->n * h->csz, 2,
-       cuda_status(launch_gram(h->dbl, h->X(), h->N, h->blk, 4 * h->N, h->n, h->gram, 4 * h->N, h->gram_work, h->st),
-                   "gram"));
+       gram_any(h, h->X(), h->N, h->blk, 4 * h->N, h->gram, 4 * h->N, h->gram_work));
   PROF(PC_SMALL, 0, 1,
        cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 0, h->prm.tol, h->sc, h->M1, h->M2, h->st),
                    "ls0"));
@@ -562,10 +613,7 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
       PROF(PC_VEC, 3.0 * cnt * h->csz, 1,
            cuda_status(launch_axpby(h->dbl, cnt, nullptr, h->G, &h->sc->beta_c, h->D(), h->st), "dir"));
     OMM_TRY(happly(h, h->D(), h->HD(), h->N, h->zero_shift, h->N, nullptr));
-    PROF(PC_GRAM, 6.0 * cnt * h->csz, 2,
-         cuda_status(launch_gram(h->dbl, h->blk, 2 * h->N, h->blk, 4 * h->N, h->n, h->gram, 4 * h->N, h->gram_work,
-                                 h->st),
-                     "gram"));
+    PROF(PC_GRAM, 6.0 * cnt * h->csz, 2, gram_any(h, h->blk, 2 * h->N, h->blk, 4 * h->N, h->gram, 4 * h->N, h->gram_work));
     PROF(PC_SMALL, 0, 1,
          cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->st),
                      "ls"));
@@ -599,13 +647,14 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
 }
 
 
-// FP64 energy E_omm and relative residual ||HX - X S^-1 K|| / ||HX|| of the current X:
+// FP64 energy E_omm and residual ||HX - X S^-1 K||_F / ||X||_F of the current X (shift
+// invariant; divided by the spectral gap it bounds the subspace angle, Davis-Kahan):
 // X converted to complex double, FP64 H-apply (shift sigma) and FP64 Grams.
 omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
   const int N = h->N;
   const size_t cnt = (size_t)N * h->n;
   if (!h->X64) {
-    OMM_TRY(h->dalloc(&h->X64, cnt * 16 * 2));   // [X | HX] in FP64
+    OMM_TRY(h->dalloc(&h->X64, cnt * 16 * 3));   // [X | HX | R] in FP64
     OMM_TRY(h->dalloc_t(&h->gram64, (size_t)N * 2 * N * sizeof(double2)));
     OMM_TRY(h->dalloc(&h->gram64_work, gram_work_bytes(N, 2 * N, h->n)));
     OMM_TRY(h->dalloc_t(&h->tmp_shift, sizeof(double2) * 2));
@@ -636,27 +685,14 @@ omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
   }
   *E = trK - 0.5 * trSK;
   if (resid) {
-    // ||HX - X S^-1 K||_F^2 = tr(HX^*HX) - tr(K^* S^-1 K) needs HX^*HX; use the residual
-    // of the Rayleigh quotient through the Gram of [X HX] with itself.
-    std::vector<double2> C2((size_t)2 * N * 2 * N);
-    OMM_TRY(ensure_dbg_work(h, gram_work_bytes(2 * N, 2 * N, h->n)));
-    if (!h->g2) OMM_TRY(h->dalloc_t(&h->g2, C2.size() * sizeof(double2)));
-    PROF(PC_GRAM, 4.0 * cnt * 16, 2,
-         cuda_status(launch_gram(true, X64, 2 * N, X64, 2 * N, h->n, h->g2, 2 * N, h->gw_dbg, h->st), "gram64b"));
-    OMM_TRY(cuda_status(cudaMemcpyAsync(C2.data(), h->g2, C2.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->st),
-                        "d2h"));
-    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
-    // S (N x N), K = X^*HX, W = HX^*HX; r^2 = tr W - tr(K^* S^-1 K)
+    // R = HX - X (S^-1 K) formed explicitly in FP64 (Rayleigh-Ritz residual), then |R|_F / |X|_F
     std::vector<cd> S((size_t)N * N), K((size_t)N * N);
-    double trW = 0.0;
-    for (int i = 0; i < N; ++i) {
-      trW += C2[(size_t)(N + i) * 2 * N + N + i].x;
+    for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j) {
-        const double2 s = C2[(size_t)i * 2 * N + j], k = C2[(size_t)i * 2 * N + N + j];
-        S[(size_t)i * N + j] = cd(s.x, s.y);
-        K[(size_t)i * N + j] = cd(k.x, k.y);
+        const double2 sv = C[(size_t)i * 2 * N + j], kv = C[(size_t)i * 2 * N + N + j];
+        S[(size_t)i * N + j] = cd(sv.x, sv.y);
+        K[(size_t)i * N + j] = cd(kv.x, kv.y);
       }
-    }
     // solve S Y = K by Gaussian elimination with partial pivoting (N x N, host)
     std::vector<cd> A(S), Y(K);
     for (int c = 0; c < N; ++c) {
@@ -678,14 +714,26 @@ omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
     }
     for (int c = N - 1; c >= 0; --c)
       for (int j = 0; j < N; ++j) {
-        cd s = Y[(size_t)c * N + j];
-        for (int k = c + 1; k < N; ++k) s -= A[(size_t)c * N + k] * Y[(size_t)k * N + j];
-        Y[(size_t)c * N + j] = s / A[(size_t)c * N + c];
+        cd sacc = Y[(size_t)c * N + j];
+        for (int k = c + 1; k < N; ++k) sacc -= A[(size_t)c * N + k] * Y[(size_t)k * N + j];
+        Y[(size_t)c * N + j] = sacc / A[(size_t)c * N + c];
       }
-    double trKY = 0.0;   // tr(K^* Y) = sum_ij conj(K_ij) Y_ij
-    for (size_t e = 0; e < (size_t)N * N; ++e) trKY += (std::conj(K[e]) * Y[e]).real();
-    const double r2 = std::max(0.0, trW - trKY);
-    *resid = std::sqrt(r2 / std::max(trW, 1e-300));
+    std::vector<cd> Mh((size_t)2 * N * N, cd(0.0, 0.0));   // [ -Y | 0 ]
+    for (size_t e = 0; e < (size_t)N * N; ++e) Mh[e] = -Y[e];
+    if (!h->m64) OMM_TRY(h->dalloc(&h->m64, (size_t)2 * N * N * 16 + 2 * sizeof(double)));
+    OMM_TRY(cuda_status(cudaMemcpyAsync(h->m64, Mh.data(), Mh.size() * 16, cudaMemcpyHostToDevice, h->st), "M"));
+    void* R64 = (char*)h->X64 + 2 * cnt * 16;
+    const double2* M1 = (const double2*)h->m64;
+    const double2* M2 = M1 + (size_t)N * N;
+    double* nrm = (double*)((char*)h->m64 + (size_t)2 * N * N * 16);
+    PROF(PC_BLOCKUPD, 3.0 * cnt * 16, 1,
+         cuda_status(launch_block_update(true, X64, HX64, M1, M2, 0.0, 1.0, N, h->n, R64, h->st), "resid"));
+    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, R64, R64, nrm, h->red_work, h->st), "dot"));
+    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, X64, X64, nrm + 1, h->red_work, h->st), "dot"));
+    double nr[2] = {0.0, 0.0};
+    OMM_TRY(cuda_status(cudaMemcpyAsync(nr, nrm, sizeof(nr), cudaMemcpyDeviceToHost, h->st), "d2h"));
+    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
+    *resid = std::sqrt(nr[0] / std::max(nr[1], 1e-300));
   }
   return OMM_OK;
 }
@@ -715,6 +763,12 @@ omm_status build_spp(omm_ctx* h) {
     OMM_TRY(upload_vec(h, &h->d_cidx, s.contrib_idx));
     OMM_TRY(upload_vec(h, &h->d_fblocks, s.fblocks));
     OMM_TRY(upload_vec(h, &h->d_bblocks, s.bblocks));
+    OMM_TRY(upload_vec(h, &h->d_leaf_nodes, s.leaf_nodes));
+    OMM_TRY(upload_vec(h, &h->d_leaf_voff, s.leaf_voff));
+    OMM_TRY(upload_vec(h, &h->d_leaf_ioff_bs, s.leaf_ioff_bs));
+    OMM_TRY(upload_vec(h, &h->d_leaf_ioff_sb, s.leaf_ioff_sb));
+    OMM_TRY(upload_vec(h, &h->d_leaf_bs_idx, s.leaf_bs_idx));
+    OMM_TRY(upload_vec(h, &h->d_leaf_sb_idx, s.leaf_sb_idx));
     OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
     h->spp_built = true;
   }
@@ -756,6 +810,7 @@ omm_status omm_default_params(omm_params* p) {
   p->tol = 1e-13;
   p->maxit = 50;
   p->refilter = 0;
+  p->gram_tensor = 0;
   return OMM_OK;
 }
 
@@ -921,6 +976,7 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
       const long long fs = h->spp.factor_size;
       if (h->Pfac < P) {
         OMM_TRY(h->dalloc(&h->factor, (size_t)P * fs * h->csz));
+        OMM_TRY(h->dalloc(&h->leafvals, (size_t)P * h->spp.leaf_size * h->csz));
         OMM_TRY(h->dalloc(&h->ubuf, (size_t)h->spp.urows * P * h->N * h->csz));
         OMM_TRY(h->dalloc(&h->ynd, (size_t)P * h->N * n * h->csz));
         h->Pfac = P;
@@ -928,6 +984,11 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
       std::vector<cd> fall((size_t)P * fs);
       for (int j = 0; j < P; ++j) std::copy(h->spp_poles[j].factor.begin(), h->spp_poles[j].factor.end(), fall.begin() + (size_t)j * fs);
       OMM_TRY(upload_complex(h, h->factor, fall, h->dbl));
+      const long long ls = h->spp.leaf_size;
+      std::vector<cd> lall((size_t)P * ls);
+      for (int j = 0; j < P; ++j)
+        std::copy(h->spp_poles[j].leafval.begin(), h->spp_poles[j].leafval.end(), lall.begin() + (size_t)j * ls);
+      OMM_TRY(upload_complex(h, h->leafvals, lall, h->dbl));
     } else {
       std::vector<cd> gh;
       for (int j = 0; j < P; ++j) {
@@ -1027,8 +1088,8 @@ omm_status omm_apply_h(omm_t h, const void* X, void* Y, int ncols, double s_re, 
 omm_status omm_gram(omm_t h, const void* A, int na, const void* B, int nb, void* C) {
   if (!h || !A || !B || !C || na < 1 || nb < 1) return OMM_EINVAL;
   OMM_TRY(ensure_dbg_work(h, gram_work_bytes(na, nb, h->n)));
-  OMM_TRY(cuda_status(launch_gram(h->dbl, A, na, B, nb, h->n, (double2*)C, nb, h->gw_dbg, h->st), "gram"));
-  return cuda_status(cudaStreamSynchronize(h->st), "sync");
+  OMM_TRY(gram_any(h, A, na, B, nb, (double2*)C, nb, h->gw_dbg));
+  return read_scalars(h);
 }
 
 omm_status omm_gradient(omm_t h, const void* X, void* HX, void* Grad) {
@@ -1055,8 +1116,7 @@ omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double*
   OMM_TRY(cuda_status(cudaMemcpyAsync(h->D(), D, cnt * h->csz, cudaMemcpyDeviceToDevice, h->st), "D"));
   OMM_TRY(happly(h, h->X(), h->HX(), h->N, h->zero_shift, h->N, nullptr));
   OMM_TRY(happly(h, h->D(), h->HD(), h->N, h->zero_shift, h->N, nullptr));
-  OMM_TRY(cuda_status(
-      launch_gram(h->dbl, h->blk, 2 * h->N, h->blk, 4 * h->N, h->n, h->gram, 4 * h->N, h->gram_work, h->st), "gram"));
+  OMM_TRY(gram_any(h, h->blk, 2 * h->N, h->blk, 4 * h->N, h->gram, 4 * h->N, h->gram_work));
   OMM_TRY(cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->st),
                       "ls"));
   OMM_TRY(read_scalars(h));
@@ -1077,7 +1137,8 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
   TrsvArgs a = trsv_args(h, ncols, (size_t)ncols);
   TrsvLevels lv = trsv_levels(h);
   const void* f = (char*)h->factor + (size_t)pole * h->spp.factor_size * h->csz;
-  OMM_TRY(cuda_status(launch_spp_solve(h->dbl, a, lv, 1, h->tv, h->ynd, h->ubuf, U, f, nullptr, h->trsv_smem, h->st),
+  OMM_TRY(cuda_status(launch_spp_solve(h->dbl, a, lv, leaf_args(h, pole), 1, h->tv, h->ynd, h->ubuf, U, f, nullptr,
+                                       h->trsv_smem, h->st),
                       "spp"));
   return cuda_status(cudaStreamSynchronize(h->st), "sync");
 }

@@ -298,6 +298,58 @@ SppStructure spp_build_structure(int dim, int m, int r) {
   for (int rr = 0; rr < st.n; ++rr) st.contrib_ptr[rr + 1] = st.contrib_ptr[rr] + (int)rows[rr].size();
   st.contrib_idx.reserve(st.contrib_ptr[st.n]);
   for (int rr = 0; rr < st.n; ++rr) st.contrib_idx.insert(st.contrib_idx.end(), rows[rr].begin(), rows[rr].end());
+  // leaf data: bandwidth from the stencil couplings inside each leaf, halo couplings
+  {
+    std::vector<int> ischild(nn, 0);
+    for (int i = 0; i < nn; ++i) {
+      if (bd.node_children_a[i] >= 0) ischild[i] = 1;
+      if (bd.node_children_b[i] >= 0) ischild[i] = 1;
+    }
+    auto cheb = [&](int p, int q) {
+      int d = 0;
+      int pc[3] = {p % m, (p / m) % m, dim == 3 ? p / (m * m) : 0};
+      int qc[3] = {q % m, (q / m) % m, dim == 3 ? q / (m * m) : 0};
+      for (int a = 0; a < dim; ++a) {
+        int t = std::abs(pc[a] - qc[a]);
+        t = std::min(t, m - t);
+        d = std::max(d, t);
+      }
+      return d;
+    };
+    long long vo = 0;
+    for (int i = 0; i < nn; ++i) {
+      if (bd.node_children_a[i] >= 0 || bd.node_children_b[i] >= 0) continue;
+      const SppNode& nd = st.nodes[i];
+      int bw = 0;
+      for (int a = 0; a < nd.ns; ++a)
+        for (int b2 = 0; b2 < nd.ns; ++b2)
+          if (cheb(st.perm[nd.off + a], st.perm[nd.off + b2]) <= r) bw = std::max(bw, std::abs(a - b2));
+      st.leaf_bw = std::max(st.leaf_bw, bw);
+    }
+    for (int i = 0; i < nn; ++i) {
+      if (bd.node_children_a[i] >= 0 || bd.node_children_b[i] >= 0) continue;
+      const SppNode& nd = st.nodes[i];
+      st.leaf_nodes.push_back(i);
+      st.leaf_voff.push_back(vo);
+      vo += (long long)nd.ns * st.leaf_bw + (long long)nd.ns * (st.leaf_bw + 1) + (long long)nd.nb * SppStructure::NBR +
+            (long long)nd.ns * SppStructure::NBR;
+      st.leaf_ioff_bs.push_back((int)st.leaf_bs_idx.size());
+      for (int j = 0; j < nd.nb; ++j) {
+        int t = 0;
+        for (int a = 0; a < nd.ns && t < SppStructure::NBR; ++a)
+          if (cheb(st.bnat[nd.boff + j], st.perm[nd.off + a]) <= r) { st.leaf_bs_idx.push_back(a); ++t; }
+        for (; t < SppStructure::NBR; ++t) st.leaf_bs_idx.push_back(-1);
+      }
+      st.leaf_ioff_sb.push_back((int)st.leaf_sb_idx.size());
+      for (int a = 0; a < nd.ns; ++a) {
+        int t = 0;
+        for (int j = 0; j < nd.nb && t < SppStructure::NBR; ++j)
+          if (cheb(st.perm[nd.off + a], st.bnat[nd.boff + j]) <= r) { st.leaf_sb_idx.push_back(j); ++t; }
+        for (; t < SppStructure::NBR; ++t) st.leaf_sb_idx.push_back(-1);
+      }
+    }
+    st.leaf_size = vo;
+  }
   // stencil offsets, x fastest
   const int rz = dim == 3 ? r : 0;
   for (int dz = -rz; dz <= rz; ++dz)
@@ -387,6 +439,7 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
   auto pval = [&](int row, int t) { return out.q[t] + qg[t] * (V[neighbor(row, t)] - lmean); };
   // ---- multifrontal LU
   out.factor.assign((size_t)st.factor_size, cd(0.0, 0.0));
+  out.leafval.assign((size_t)st.leaf_size, cd(0.0, 0.0));
   out.pivot_min = 1e300;
   out.pivot_max = 0.0;
   out.nperturbed = 0;
@@ -425,6 +478,9 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
       }
       std::vector<cd>().swap(upd[c]);
     }
+    const bool leaf = children[s].empty();
+    std::vector<cd> F0;
+    if (leaf) F0 = F;   // original couplings of the leaf (no children: F holds only P's entries)
     // partial LU of the first ns rows / columns
     for (int k = 0; k < ns; ++k) {
       cd piv = F[(size_t)k * nf + k];
@@ -486,6 +542,37 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
         for (int k = i; k < ns; ++k) acc += Ui[(size_t)i * ns + k] * F[(size_t)k * nf + ns + j];
         wb[(size_t)i * kb + ns + j] = -acc;
       }
+    }
+    if (leaf) {
+      const int bw = st.leaf_bw, NB = SppStructure::NBR;
+      const size_t li = std::lower_bound(st.leaf_nodes.begin(), st.leaf_nodes.end(), s) - st.leaf_nodes.begin();
+      cd* v = &out.leafval[st.leaf_voff[li]];
+      cd* Lb = v;
+      cd* Ub = Lb + (size_t)ns * bw;
+      cd* Fbs = Ub + (size_t)ns * (bw + 1);
+      cd* Fsb = Fbs + (size_t)nb * NB;
+      for (int i = 0; i < ns; ++i) {
+        for (int t = 0; t < bw; ++t) {
+          const int j = i - 1 - t;
+          Lb[(size_t)i * bw + t] = j >= 0 ? F[(size_t)i * nf + j] : cd(0.0, 0.0);
+        }
+        for (int t = 0; t <= bw; ++t) {
+          const int j = i + t;
+          Ub[(size_t)i * (bw + 1) + t] = j < ns ? (t == 0 ? 1.0 / F[(size_t)i * nf + i] : F[(size_t)i * nf + j]) : cd(0.0, 0.0);
+        }
+      }
+      const int* bsi = &st.leaf_bs_idx[st.leaf_ioff_bs[li]];
+      for (int j = 0; j < nb; ++j)
+        for (int t = 0; t < NB; ++t) {
+          const int i = bsi[j * NB + t];
+          Fbs[(size_t)j * NB + t] = i >= 0 ? F0[(size_t)(ns + j) * nf + i] : cd(0.0, 0.0);
+        }
+      const int* sbi = &st.leaf_sb_idx[st.leaf_ioff_sb[li]];
+      for (int i = 0; i < ns; ++i)
+        for (int t = 0; t < NB; ++t) {
+          const int j = sbi[i * NB + t];
+          Fsb[(size_t)i * NB + t] = j >= 0 ? F0[(size_t)i * nf + ns + j] : cd(0.0, 0.0);
+        }
     }
     upd[s].resize((size_t)nb * nb);
     for (int i = 0; i < nb; ++i)

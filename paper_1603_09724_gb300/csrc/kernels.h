@@ -29,6 +29,13 @@ cudaError_t launch_greenq_big(bool dbl, int dim, int m, const void* B, void* Out
 size_t gram_work_bytes(int na, int nb, size_t n);
 cudaError_t launch_gram(bool dbl, const void* A, int na, const void* B, int nb, size_t n, double2* C, int ldc,
                         void* work, cudaStream_t st);
+// ---- k_gram_tc.cu: the same Gram on tcgen05 tensor cores (complex64 inputs, TF32 x 3 split,
+// FP32 accumulation in tensor memory, FP64 split-K sum).  err: device flag set to 1 if a
+// bounded wait gave up.
+bool gram_tc_supported(size_t n);
+size_t gram_tc_work_bytes(int na, int nb, size_t n);
+cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t n, double2* C, int ldc, void* work,
+                           int* err, cudaStream_t st);
 // Out = a*A + b*B + A*M1 + B*M2 (A, B: n x N blocks; M1, M2: N x N complex, working precision,
 // row-major, in device memory; a, b real).
 cudaError_t launch_block_update(bool dbl, const void* A, const void* B, const void* M1, const void* M2,

@@ -43,11 +43,23 @@ struct SppStructure {
   std::vector<int> fblocks, bblocks;
   std::vector<int> fstart, fcount, bstart, bcount;
   std::vector<int> fkmax, bkmax;   // per level: largest K of the forward / backward products
+  // leaves (height 0, no children): banded L, U and the original sparse coupling to the halo
+  int leaf_bw = 0;                 // bandwidth of the leaf LU in the leaf's own (x-fastest) order
+  static constexpr int NBR = 9;    // max couplings of one unknown (the 3^2 stencil)
+  std::vector<int> leaf_nodes;     // node ids of the leaves
+  std::vector<long long> leaf_voff;// per leaf: offset of its values in a pole's leaf array
+  std::vector<int> leaf_ioff_bs;   // per leaf: offset into leaf_bs_idx (nb * NBR)
+  std::vector<int> leaf_ioff_sb;   // per leaf: offset into leaf_sb_idx (ns * NBR)
+  std::vector<int> leaf_bs_idx;    // halo row j -> leaf columns i coupled by P (or -1)
+  std::vector<int> leaf_sb_idx;    // leaf row i -> halo columns j coupled by P (or -1)
+  long long leaf_size = 0;         // complex values per pole: per leaf L band (ns*bw),
+                                   // U band with inverted diagonal (ns*(bw+1)), F_BS (nb*NBR), F_SB (ns*NBR)
 };
 
 struct SppPole {
   std::vector<cd> q;            // stencil row (|a| entries, same order as offsets)
   std::vector<cd> factor;       // per node W_f and W_b (see SppNode)
+  std::vector<cd> leafval;      // per leaf banded factors and couplings (see SppStructure)
   double pivot_min = 0, pivot_max = 0;
   int nperturbed = 0;
   double sigma_min = 0, sigma_max = 0;   // singular values of G(a, a^c)

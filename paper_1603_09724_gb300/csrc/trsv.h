@@ -33,9 +33,26 @@ struct TrsvLevels {
   std::vector<int> fkmax, bkmax;                      // host, per height: shared-memory sizing
 };
 
+// Leaves: banded L and U (inverted diagonal) of the leaf front and its original sparse
+// coupling to the halo, per pole in one array (see SppStructure).
+struct LeafArgs {
+  int nleaves = 0;
+  int bw = 0;
+  int max_ns = 0;
+  const int* nodes = nullptr;
+  const long long* voff = nullptr;
+  const int* ioff_bs = nullptr;
+  const int* ioff_sb = nullptr;
+  const int* bs_idx = nullptr;
+  const int* sb_idx = nullptr;
+  long long leaf_size = 0;
+  const void* vals = nullptr;   // P * leaf_size complex values
+};
+
 size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb);
 // b (natural, S systems) -> x (natural); ynd, u work buffers.  factor: P poles' blocks.
-cudaError_t launch_spp_solve(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, int P, const void* b, void* ynd,
-                             void* u, void* x, const void* factor, const int* active, size_t smem, cudaStream_t st);
+cudaError_t launch_spp_solve(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
+                             const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
+                             size_t smem, cudaStream_t st);
 
 }  // namespace omm

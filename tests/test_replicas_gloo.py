@@ -1,0 +1,36 @@
+"""The multi-GPU form is replicas only (independent solves per GPU, no data-path
+collective): bench.py takes the slowest rank's timed region and counts every rank's
+solves.  Checked here with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms, value = bench.aggregate_ranks(100.0 * (rank + 1), steps=4, world=world, device="cpu")
+    out[rank] = (ms, value)
+    dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_rank():
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        ms, value = out[r]
+        assert ms == pytest.approx(200.0)
+        assert value == pytest.approx(world * 4 / 0.2)

@@ -47,6 +47,11 @@ template <typename Cd, typename Cs> __host__ __device__ __forceinline__ Cd ccast
   Cd r; r.x = (decltype(r.x))a.x; r.y = (decltype(r.y))a.y; return r;
 }
 
+// Raise a kernel's opt-in dynamic shared-memory limit to the most the device allows
+// (given its static shared memory), once per kernel and thread-safely; the limit is a
+// ceiling only, the launch's dynamic size still sets the occupancy.
+cudaError_t raise_smem_limit(const void* func);
+
 }  // namespace omm
 
 #define OMM_CUDA_TRY(expr)                                              \

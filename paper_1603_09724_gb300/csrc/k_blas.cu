@@ -8,7 +8,27 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <map>
+#include <mutex>
+
 namespace omm {
+
+cudaError_t raise_smem_limit(const void* func) {
+  static std::mutex mu;
+  static std::map<const void*, cudaError_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(func);
+  if (it != done.end()) return it->second;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  done[func] = e;
+  return e;
+}
 
 namespace {
 constexpr int GT = 32;   // Gram tile (outputs per side)
@@ -299,7 +319,7 @@ cudaError_t launch_convert(bool to_dbl, size_t count, const void* src, void* dst
 namespace omm {
 namespace {
 constexpr size_t kNoAllocPartials = (size_t)1 << 19;   // double2 entries (8 MiB per device)
-__device__ __align__(256) double2 g_noalloc_partials[kNoAllocPartials];
+static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocPartials];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double2* g_noalloc_ptr[kMaxDevices] = {};

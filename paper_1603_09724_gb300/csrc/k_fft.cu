@@ -115,12 +115,8 @@ static cudaError_t launch_happly_t(const void* X, void* Y, int ncols, const void
                                    int cpg, const void* tw, double kin_over_n, const int* active, cudaStream_t st) {
   using G = GridCfg<T, M, D>;
   auto k = happly_kernel<T, M, D>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = raise_smem_limit((const void*)k);
+  if (e != cudaSuccess) return e;
   k<<<ncols, G::NT, G::smem, st>>>((const cx_t<T>*)X, (cx_t<T>*)Y, (const T*)V, shifts, cpg,
                                    (const cx_t<T>*)tw, kin_over_n, active);
   return cudaGetLastError();
@@ -131,12 +127,8 @@ static cudaError_t launch_greenq_t(const void* B, void* Out, int ncols, const vo
                                    int cpg, const void* tw, const int* active, cudaStream_t st) {
   using G = GridCfg<T, M, D>;
   auto k = greenq_kernel<T, M, D>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = raise_smem_limit((const void*)k);
+  if (e != cudaSuccess) return e;
   k<<<ncols, G::NT, G::smem, st>>>((const cx_t<T>*)B, (cx_t<T>*)Out, (const cx_t<T>*)ghat, (const cx_t<T>*)q, nq,
                                    cpg, (const cx_t<T>*)tw, active);
   return cudaGetLastError();

@@ -269,12 +269,8 @@ bool gram_tc_supported(size_t n) { return n % (KF / 2) == 0; }
 cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t n, double2* C, int ldc, void* work,
                            int* err, cudaStream_t st) {
   if (na <= 0 || nb <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e0 = raise_smem_limit((const void*)gram_tc_kernel);
+  if (e0 != cudaSuccess) return e0;
   int ks = tc_splits(na, nb, n);
   size_t kchunk = (n + ks - 1) / ks;
   kchunk = (kchunk + (KF / 2) - 1) / (KF / 2) * (KF / 2);

@@ -267,30 +267,17 @@ static cudaError_t run_t(const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs
                          cudaStream_t st) {
   using C = cx_t<T>;
   constexpr int RT = TrsvCfg<T>::RT;
-  const size_t stat = sizeof(C) * (2 * (size_t)KT * (RB + 1));
-  const size_t dyn = smem_total - stat;
-  // the opt-in shared-memory limit only ever grows (handles of different grids share the kernels)
-  static size_t attr_bytes = 0;
-  if (dyn > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(trsv_gemm_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  (void)smem_total;
+  for (const void* f : {(const void*)trsv_gemm_kernel<T, true>, (const void*)trsv_gemm_kernel<T, false>,
+                        (const void*)leaf_kernel<T, true>, (const void*)leaf_kernel<T, false>}) {
+    cudaError_t e = raise_smem_limit(f);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(trsv_gemm_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-    attr_bytes = dyn;
   }
   const int tiles = (a.N + RT - 1) / RT;
   const bool leaves = la.nleaves > 0;
   const size_t lsm = (size_t)la.max_ns * LT * sizeof(C);
   const dim3 lgrid(la.nleaves, P, (a.N + LT - 1) / LT);
   if (leaves) {
-    static size_t lattr = 0;
-    if (lsm > lattr) {
-      cudaError_t e = cudaFuncSetAttribute(leaf_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
-      if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(leaf_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
-      if (e != cudaSuccess) return e;
-      lattr = lsm;
-    }
     leaf_kernel<T, true><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
   }
   // dynamic shared memory sized per level (the root fronts need ~100 KB)

@@ -140,3 +140,57 @@ def small_case(m: int = 16, N: int = 8, dim: int = 2, L: float = 10.0, seed: int
     """A tiny workload for parity tests (dense oracle on n <= 4096)."""
     pot = potential if dim == 2 else "lattice3d"
     return Workload(f"small-{dim}d-{m}-{N}", dim, m, L, N, 16, pot, seed, "fp64")
+
+
+# ---- many-Hamiltonian workloads (batched and served solves)
+@dataclasses.dataclass(frozen=True)
+class HamSpec:
+    key: str
+    m: int
+    N: int
+    L: float
+    potential: str     # 'smooth2d' | 'wells2d'
+    seed: int
+
+    @property
+    def n(self) -> int:
+        return self.m * self.m
+
+    def potential_values(self) -> np.ndarray:
+        if self.potential == "smooth2d":
+            return smooth_field_2d(self.m, self.L, seed=self.seed)
+        return wells_2d(self.m, self.L, seed=self.seed)
+
+
+def batch_mix(count: int = 64, seed: int = 0) -> list:
+    """Independent 2D Hamiltonians: grid uniform from {32, 64, 96, 128}^2, N uniform in
+    [16, 128] (at most n/4), smooth random V (seed 100 + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.choice([32, 64, 96, 128]))
+        N = int(rng.integers(16, 129))
+        N = min(N, m * m // 4)
+        out.append(HamSpec(f"batch{i}", m, N, 10.0, "smooth2d", 100 + i))
+    return out
+
+
+def serving_mix(count: int = 12, seed: int = 1) -> list:
+    """Distinct Hamiltonians a request stream draws from: 2D grids from {64, 72, 96, 128}^2,
+    N uniform in [32, 128], four Gaussian wells per box (seed 200 + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.choice([64, 72, 96, 128]))
+        N = int(rng.integers(32, 129))
+        out.append(HamSpec(f"serve{i}", m, N, 10.0, "wells2d", 200 + i))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, nkeys: int, seed: int = 2):
+    """Arrival times (s) of `count` requests at `rate` per second and the Hamiltonian index
+    each one asks for (uniform over nkeys)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    keys = rng.integers(0, nkeys, size=count)
+    return t, keys

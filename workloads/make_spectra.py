@@ -17,7 +17,7 @@ import numpy as np
 
 from oracle import hamiltonian as ham
 from oracle import spectrum
-from workloads import WORKLOADS
+from workloads import WORKLOADS, batch_mix, serving_mix
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "spectra.json")
 
@@ -38,6 +38,25 @@ def compute(wl, kc=24):
                 lowest=[float(x) for x in lam])
 
 
+def compute_spec(h, kc=24, window=8):
+    """Spectral data of one many-Hamiltonian entry (dense eigh for n <= 4096, else the
+    plane-wave box).  N is taken within +-window of the drawn value where the gap
+    lam_{N+1} - lam_N is largest, so that the occupied space is well separated."""
+    V = h.potential_values()
+    shape = (h.m, h.m)
+    sig = ham.default_shift(shape, h.L, V)
+    cnt = h.N + window + 1
+    if h.n <= 4096:
+        lam = np.linalg.eigvalsh(ham.dense_h(shape, h.L, V, sig))[:cnt]
+    else:
+        lam = spectrum.lowest_eigs_kspace(shape, h.L, V, sig, cnt, kc)
+    cands = range(max(1, h.N - window), h.N + window + 1)
+    N = max(cands, key=lambda k: lam[k] - lam[k - 1])
+    return dict(sigma=sig, lam1=float(lam[0]), lamN=float(lam[N - 1]), lamN1=float(lam[N]),
+                E_ref=float(0.5 * np.sum(lam[:N])), m=h.m, N=int(N), N_drawn=h.N, potential=h.potential,
+                seed=h.seed)
+
+
 def main(names=("wells2d-32", "smooth2d-128")):
     data = {}
     if os.path.exists(OUT):
@@ -45,6 +64,10 @@ def main(names=("wells2d-32", "smooth2d-128")):
     for name in names:
         data[name] = compute(WORKLOADS[name])
         print(name, data[name]["lamN1"] - data[name]["lamN"], data[name]["method"])
+    for h in batch_mix() + serving_mix():
+        if h.key not in data:
+            data[h.key] = compute_spec(h)
+            print(h.key, h.m, h.N, data[h.key]["lamN1"] - data[h.key]["lamN"], flush=True)
     json.dump(data, open(OUT, "w"), indent=1)
 
 

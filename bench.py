@@ -33,7 +33,10 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="smooth2d-128")
+    ap.add_argument("--workload", default="smooth2d-128",
+                    help="smooth2d-128 (the default line), wells2d-32, lattice3d-48")
+    ap.add_argument("--inner", default="auto", choices=["auto", "spp", "kinetic"],
+                    help="GMRES inner preconditioner; auto: sparsifying in 2D and up to 16^3, kinetic above")
     ap.add_argument("--iters", type=int, default=0, help="fixed CG iterations (0: energy criterion)")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the untimed FP64-form comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -47,6 +50,8 @@ def args_parse():
     ap.add_argument("--requests", type=int, default=120, help="serve mode: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="batch/serve: concurrent solves")
+    ap.add_argument("--orbitals", default="real", choices=["real", "complex"],
+                    help="real: real X (eq. lst writes Y real), conjugate pole pairs folded (P/2 solves); complex: P solves")
     return ap.parse_args()
 
 
@@ -110,11 +115,21 @@ def load_workload(name):
     return wl, spectra
 
 
-def workload_config(wl, spectra, iters, precision="mixed", refilter=0, rtol=1e-5):
+def inner_choice(wl, inner="auto"):
+    if inner == "auto":
+        return "spp" if (wl.dim == 2 or wl.m <= 16) else "kinetic"
+    return inner
+
+
+def workload_config(wl, spectra, iters, precision="mixed", refilter=0, rtol=1e-5, orbitals="real", inner="auto"):
     return {"workload": f"{wl.name}: {wl.dim}D {wl.m}^{wl.dim} periodic grid (n={wl.n}), N={wl.N} states, "
                         f"P={wl.P} conformal poles, {wl.potential} potential, {precision}",
+            "orbitals": ("real X, conjugate pole pairs folded (P/2 GMRES solves per application)"
+                         if orbitals == "real" else "complex X, P GMRES solves per application"),
             "grid": [wl.m] * wl.dim, "box_len": wl.L, "N": wl.N, "P": wl.P, "precision": precision,
-            "inner_preconditioner": "sparsifying (nested-dissection multifrontal LU)",
+            "inner_preconditioner": ("sparsifying (nested-dissection multifrontal LU)"
+                                     if inner_choice(wl, inner) == "spp" else
+                                     "kinetic (T + <V> - sigma - z)^-1 (the sparsifying factor is not built above 16^3)"),
             "gmres": f"restart 15, <=5 cycles, rtol {rtol:g}", "cg_iters": iters if iters else "energy criterion",
             "refilter": refilter,
             "l2": "inputs/working set larger than L2 (GMRES basis ~GBs)", "parallelism": "replicas",
@@ -133,7 +148,8 @@ def oracle_sample(wl, spectra, budget_s=12.0):
     z, w = opoles.poles_conformal(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
     X0 = wl.initial_block()
     cols = 2
-    pc = PolePreconditioner(wl.shape, wl.L, V, spectra["sigma"], z[:1], w[:1], mode="gmres", inner="spp")
+    pc = PolePreconditioner(wl.shape, wl.L, V, spectra["sigma"], z[:1], w[:1], mode="gmres",
+                            inner="spp" if inner_choice(wl) == "spp" else "lap")
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -179,10 +195,11 @@ def run_reference(a):
     rec = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(wl, spectra, a.iters, "fp64 oracle"),
+           "config": workload_config(wl, spectra, a.iters, "fp64 oracle", orbitals=a.orbitals, inner=a.inner),
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                             "sample": f"each step: one oracle pole solve (1 pole x 2 columns, ~4 s), extrapolated "
-                                      f"to P*N systems x {applications} applications per solve; wall {wall:.1f} s"},
+                                      f"to P*N systems x {applications} applications per solve (the oracle solves every pole, "
+                                      f"no conjugate folding); wall {wall:.1f} s"},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(rec))
 
@@ -226,12 +243,15 @@ def run_ours(a):
     z, w = omm.poles_fermi(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
     tol = 0.0 if a.iters else (1e-10 if mixed else 1e-13)
     maxit = a.iters if a.iters else 40
-    prm = omm.default_params(precision=prec, maxit=maxit, tol=tol, refilter=a.refilter, gmres_rtol=a.rtol)
+    real = a.orbitals == "real"
+    inner = omm.OMM_INNER_SPARSIFY if inner_choice(wl, a.inner) == "spp" else omm.OMM_INNER_KINETIC
+    prm = omm.default_params(precision=prec, maxit=maxit, tol=tol, refilter=a.refilter, gmres_rtol=a.rtol,
+                             real_orbitals=int(real), inner=inner)
     s = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
     t_setup = time.perf_counter()
     s.set_poles(z, w)
     t_setup = time.perf_counter() - t_setup
-    X0h = torch.from_numpy(wl.initial_block(np.complex64 if mixed else np.complex128)).pin_memory()
+    X0h = torch.from_numpy(wl.initial_block(np.complex64 if mixed else np.complex128, real=real)).pin_memory()
     X0 = X0h.to("cuda")
     stream = torch.cuda.current_stream()
 
@@ -295,7 +315,8 @@ def run_ours(a):
     rec = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64" if mixed else "c128", "data": "synthetic",
-           "config": workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64", a.refilter, a.rtol),
+           "config": workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64", a.refilter, a.rtol,
+                                     a.orbitals, a.inner),
            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
            "solve": {"iters": st["iters"], "filters": st["filters"], "converged": st["converged"],
                      "energy_fp64": st["energy_fp64"], "resid_fp64": st["resid_fp64"],
@@ -335,12 +356,16 @@ def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w):
     import numpy as np
     try:
         Xm = s.get_orbitals().cpu().numpy().astype(np.complex128)
+        real = a.orbitals == "real"
         prm = omm.default_params(precision=omm.OMM_FP64, maxit=a.iters if a.iters else 40,
-                                 tol=0.0 if a.iters else 1e-13, refilter=a.refilter, gmres_rtol=a.rtol)
+                                 tol=0.0 if a.iters else 1e-13, refilter=a.refilter, gmres_rtol=a.rtol,
+                                 real_orbitals=int(real),
+                                 inner=omm.OMM_INNER_SPARSIFY if inner_choice(wl, a.inner) == "spp"
+                                 else omm.OMM_INNER_KINETIC)
         t0 = time.perf_counter()
         s64 = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
         s64.set_poles(z, w)
-        s64.set_orbitals(torch.from_numpy(wl.initial_block(np.complex128)).to("cuda"))
+        s64.set_orbitals(torch.from_numpy(wl.initial_block(np.complex128, real=real)).to("cuda"))
         st = s64.solve()
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
@@ -374,7 +399,8 @@ def run_many(a):
                        sigma=sp["sigma"], P=16)
 
     free, total = torch.cuda.mem_get_info()
-    srv = OmmServer(hbm_budget=int(0.85 * free), slots=a.slots, gmres_rtol=a.rtol)
+    srv = OmmServer(hbm_budget=int(0.85 * free), slots=a.slots, gmres_rtol=a.rtol,
+                    real_orbitals=int(a.orbitals == "real"))
     clocks = ClockSampler(0)
     clocks.start()
     t0 = time.perf_counter()
@@ -412,7 +438,7 @@ def run_many(a):
     rec = {"mode": a.mode, "metric": METRIC, "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
            "higher_is_better": True, "data": "synthetic", "dtype": "c64",
            "config": {"workload": cfg, "slots": a.slots, "hbm_budget_GB": round(0.85 * free / 2**30, 1),
-                      "gmres_rtol": a.rtol},
+                      "gmres_rtol": a.rtol, "orbitals": a.orbitals},
            "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"]}, "requests": summ["requests"],
            "warm_fraction": summ["warm_fraction"], "wall_s": wall,
            "E_rel_err_vs_exact": {"max": max(errs), "median": float(np.median(errs))},

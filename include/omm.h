@@ -83,6 +83,14 @@ typedef struct {
   int refilter;         /* extra (filter + CG) rounds after the first                  */
   int gram_tensor;      /* 1: complex64 Grams on tcgen05 tensor cores (TF32 x 3 split,
                            FP64 split-K sum); 0: CUDA cores.  FP64 handles use CUDA cores */
+  int real_orbitals;    /* 1: X is kept real (H is real symmetric with the symmetric
+                           kinetic symbol, and Sec. 3.1 writes the pole solutions real).  omm_set_poles then folds
+                           each conjugate pair (z, w), (conj z, conj w) into one solve:
+                           w Y + conj(w Y) = 2 Re(w Y) for real right-hand sides, so the
+                           pole expansion costs P/2 GMRES solves; poles must come in
+                           conjugate pairs (or be real with real weight), else
+                           omm_set_poles returns OMM_EINVAL.  omm_set_orbitals drops the
+                           imaginary part of the block.  0: complex X, P solves.       */
 } omm_params;
 
 typedef struct {

@@ -36,3 +36,33 @@ def lowest_eigs_kspace(shape, L, V, shift, count, kc):
     Hk = Vh[didx] + np.diag(Tk) - shift * np.eye(len(ks))
     lam = np.linalg.eigvalsh(Hk)
     return lam[:count]
+
+
+def lowest_eigs_bloch(shape, L, V, shift, cells, count):
+    """Exact lowest eigenvalues of the grid H for a potential periodic on a lattice of
+    `cells` cells per axis (each cell mc = m / cells grid points wide).
+
+    V(x + mc e_a) = V(x) makes Vh(q) vanish unless every component of q is a multiple of
+    `cells`, so H(k, k') (above) couples k and k' only when k = k' (mod cells) in every
+    component.  The DFT grid splits into cells^d Bloch sectors r (k = r + cells * j,
+    j in [0, mc)^d), each a dense mc^d x mc^d Hermitian block; the union of the blocks'
+    spectra is the spectrum of H, with no truncation.  Used for the 48^3 lattice workload
+    (64 blocks of 1728)."""
+    d = len(shape)
+    m = shape[0]
+    assert all(mi == m for mi in shape) and m % cells == 0
+    mc = m // cells
+    n = m ** d
+    Vg = np.asarray(V).reshape((m,) * d)                                  # axes (z, y, x)
+    Vh = np.fft.fftn(Vg) / n
+    T = kinetic_symbol(shape, L).reshape((m,) * d)
+    J = np.array([tuple(reversed(t)) for t in itertools.product(range(mc), repeat=d)])   # (jx, jy[, jz])
+    lams = []
+    for r in itertools.product(range(cells), repeat=d):
+        K = np.asarray(r[::-1])[None, :] + cells * J                     # DFT indices (kx, ky[, kz]) in [0, m)
+        Tk = T[tuple(K[:, a] for a in range(d))[::-1]]
+        diff = (K[:, None, :] - K[None, :, :]) % m
+        Hr = Vh[tuple(diff[..., a] for a in range(d))[::-1]] + np.diag(Tk - shift)
+        lams.append(np.linalg.eigvalsh(Hr))
+    lam = np.sort(np.concatenate(lams))
+    return lam[:count]

@@ -40,6 +40,8 @@ void omm_internal_set_cuda_error(cudaError_t e, const char* what, const char* fi
   g_last_error = std::string(cudaGetErrorString(e)) + " in " + what + " (" + file + ":" + std::to_string(line) + ")";
 }
 
+static void omm_internal_set_message(const char* msg) { g_last_error = msg; }
+
 enum ProfClass { PC_HAPPLY = 0, PC_GREENQ, PC_TRSV, PC_ORTH, PC_GRAM, PC_BLOCKUPD, PC_VEC, PC_SMALL, PC_NCLS };
 const char* const kProfNames[PC_NCLS] = {"happly", "greenq", "trsv", "orth", "gram", "block_update", "vector", "small"};
 
@@ -109,7 +111,8 @@ struct omm_ctx {
 
   // poles
   int P = 0;
-  std::vector<double2> z, w;
+  std::vector<double2> z, w;   // the poles solved (conjugate pairs folded for real orbitals)
+  bool real_combine = false;   // pole sum keeps 2 Re(w Y) of each folded pair
   bool poles_set = false;
   // GMRES work (sized for P poles)
   int Palloc = 0;
@@ -159,6 +162,8 @@ struct omm_ctx {
   int* d_leaf_sb_idx = nullptr;
   void* leafvals = nullptr;     // P * leaf_size complex
   int* d_bblocks = nullptr;
+  int* d_lunk = nullptr;                    // unknowns of each tree height (ND indices)
+  std::vector<int> lunk_start, lunk_count;
   size_t trsv_smem = 0;
   int last_gmres_max = 0;
   double last_relres_max = 0.0;
@@ -423,7 +428,10 @@ LeafArgs leaf_args(omm_ctx* h, int pole_base) {
   const SppStructure& s = h->spp;
   la.nleaves = (int)s.leaf_nodes.size();
   la.bw = s.leaf_bw;
-  for (int id : s.leaf_nodes) la.max_ns = std::max(la.max_ns, s.nodes[id].ns);
+  for (int id : s.leaf_nodes) {
+    la.max_ns = std::max(la.max_ns, s.nodes[id].ns);
+    la.max_nb = std::max(la.max_nb, s.nodes[id].nb);
+  }
   la.nodes = h->d_leaf_nodes;
   la.voff = h->d_leaf_voff;
   la.ioff_bs = h->d_leaf_ioff_bs;
@@ -446,6 +454,9 @@ TrsvLevels trsv_levels(omm_ctx* h) {
   lv.bcount = h->spp.bcount;
   lv.fkmax = h->spp.fkmax;
   lv.bkmax = h->spp.bkmax;
+  lv.lunk = h->d_lunk;
+  lv.ustart = h->lunk_start;
+  lv.ucount = h->lunk_count;
   return lv;
 }
 
@@ -462,7 +473,9 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   TrsvLevels lv = trsv_levels(h);
   const double bytes = ((double)P * h->spp.factor_size + (4.0 * h->n + 2.0 * h->spp.urows) * (double)S) * h->csz;
   int nk = 0;
-  for (int l = 0; l < lv.nlevels; ++l) nk += (lv.fcount[l] > 0) + (lv.bcount[l] > 0);
+  const bool has_leaves = !h->spp.leaf_nodes.empty();
+  for (int l = 0; l < lv.nlevels; ++l)   // per height: (assembly +) product forward, product backward
+    nk += (lv.fcount[l] > 0) * (1 + ((l > 0 || !has_leaves) && lv.ucount[l] > 0)) + (lv.bcount[l] > 0);
   PROF(PC_TRSV, bytes, nk,
        cuda_status(launch_spp_solve(h->dbl, a, lv, leaf_args(h, 0), P, tmp, h->ynd, h->ubuf, Z, h->factor, active,
                                     h->trsv_smem, h->st),
@@ -534,7 +547,7 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
                      "update"));
   }
   PROF(PC_VEC, (double)(d.S + N) * h->n * h->csz, 1,
-       cuda_status(launch_pole_combine(h->dbl, d, P, h->wts, sign, h->xs, out, h->st), "combine"));
+       cuda_status(launch_pole_combine(h->dbl, d, P, h->wts, sign, h->real_combine, h->xs, out, h->st), "combine"));
   return OMM_OK;
 }
 
@@ -763,6 +776,18 @@ omm_status build_spp(omm_ctx* h) {
     OMM_TRY(upload_vec(h, &h->d_cidx, s.contrib_idx));
     OMM_TRY(upload_vec(h, &h->d_fblocks, s.fblocks));
     OMM_TRY(upload_vec(h, &h->d_bblocks, s.bblocks));
+    {
+      std::vector<int> lunk;
+      h->lunk_start.assign(s.levels.size(), 0);
+      h->lunk_count.assign(s.levels.size(), 0);
+      for (size_t lh = 0; lh < s.levels.size(); ++lh) {
+        h->lunk_start[lh] = (int)lunk.size();
+        for (int id : s.levels[lh])
+          for (int i = 0; i < s.nodes[id].ns; ++i) lunk.push_back(s.nodes[id].off + i);
+        h->lunk_count[lh] = (int)lunk.size() - h->lunk_start[lh];
+      }
+      OMM_TRY(upload_vec(h, &h->d_lunk, lunk));
+    }
     OMM_TRY(upload_vec(h, &h->d_leaf_nodes, s.leaf_nodes));
     OMM_TRY(upload_vec(h, &h->d_leaf_voff, s.leaf_voff));
     OMM_TRY(upload_vec(h, &h->d_leaf_ioff_bs, s.leaf_ioff_bs));
@@ -811,6 +836,7 @@ omm_status omm_default_params(omm_params* p) {
   p->maxit = 50;
   p->refilter = 0;
   p->gram_tensor = 0;
+  p->real_orbitals = 0;
   return OMM_OK;
 }
 
@@ -935,8 +961,51 @@ void omm_destroy(omm_t h) {
   delete h;
 }
 
+// Real orbitals: (H - conj z)^-1 R = conj((H - z)^-1 R) for real H and R, so a conjugate
+// pair contributes w Y + conj(w Y) = 2 Re(w Y) and one solve of the pair suffices.
+// Returns the kept poles (2 w for a pair, w for a real pole) or false if some pole has
+// no conjugate partner.
+static bool fold_conjugate_pairs(int P, const double* z, const double* w, std::vector<double>& zk,
+                                 std::vector<double>& wk) {
+  std::vector<char> used(P, 0);
+  zk.clear();
+  wk.clear();
+  auto close = [](double a, double b, double scale) { return std::fabs(a - b) <= 1e-10 * scale; };
+  for (int j = 0; j < P; ++j) {
+    if (used[j]) continue;
+    used[j] = 1;
+    const double zs = std::hypot(z[2 * j], z[2 * j + 1]) + 1e-300, ws = std::hypot(w[2 * j], w[2 * j + 1]) + 1e-300;
+    if (close(z[2 * j + 1], 0.0, zs) && close(w[2 * j + 1], 0.0, ws)) {   // real pole, real weight
+      zk.insert(zk.end(), {z[2 * j], 0.0});
+      wk.insert(wk.end(), {w[2 * j], 0.0});
+      continue;
+    }
+    int k = -1;
+    for (int t = j + 1; t < P && k < 0; ++t)
+      if (!used[t] && close(z[2 * t], z[2 * j], zs) && close(z[2 * t + 1], -z[2 * j + 1], zs) &&
+          close(w[2 * t], w[2 * j], ws) && close(w[2 * t + 1], -w[2 * j + 1], ws))
+        k = t;
+    if (k < 0) return false;
+    used[k] = 1;
+    zk.insert(zk.end(), {z[2 * j], z[2 * j + 1]});
+    wk.insert(wk.end(), {2.0 * w[2 * j], 2.0 * w[2 * j + 1]});
+  }
+  return true;
+}
+
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
   if (!h || !z || !w || P < 1 || P > PMAX) return OMM_EINVAL;
+  std::vector<double> zf, wf;
+  if (h->prm.real_orbitals) {
+    if (!fold_conjugate_pairs(P, z, w, zf, wf)) {
+      omm_internal_set_message("real_orbitals: a pole has no conjugate partner");
+      return OMM_EINVAL;
+    }
+    P = (int)zf.size() / 2;
+    z = zf.data();
+    w = wf.data();
+  }
+  h->real_combine = h->prm.real_orbitals != 0;
   h->P = P;
   h->z.resize(P);
   h->w.resize(P);
@@ -1012,7 +1081,9 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
 
 omm_status omm_set_orbitals(omm_t h, const void* X) {
   if (!h || !X) return OMM_EINVAL;
-  return cuda_status(cudaMemcpyAsync(h->X(), X, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "set X");
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->X(), X, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "set X"));
+  if (h->prm.real_orbitals) return cuda_status(launch_real_part(h->dbl, (size_t)h->N * h->n, h->X(), h->st), "real X");
+  return OMM_OK;
 }
 
 omm_status omm_get_orbitals(omm_t h, void* X) {

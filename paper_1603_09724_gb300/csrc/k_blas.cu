@@ -307,6 +307,22 @@ cudaError_t launch_convert(bool to_dbl, size_t count, const void* src, void* dst
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void real_part_kernel(size_t count, cx_t<T>* __restrict__ x) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    x[e].y = 0;
+}
+
+cudaError_t launch_real_part(bool dbl, size_t count, void* x, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const int blocks = (int)((count + 255) / 256 < 4864 ? (count + 255) / 256 : 4864);
+  if (dbl)
+    real_part_kernel<double><<<blocks, 256, 0, st>>>(count, (double2*)x);
+  else
+    real_part_kernel<float><<<blocks, 256, 0, st>>>(count, (float2*)x);
+  return cudaGetLastError();
+}
+
 }  // namespace omm
 
 // ------------------------------------------------------------------ Gram without device allocation

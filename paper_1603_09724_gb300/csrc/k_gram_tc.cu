@@ -204,8 +204,10 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(const float* __rest
     __syncthreads();
     if (abort_sh) break;
   }
-  // ---- epilogue: TMEM lane = row of C, column = [Re | Im] index
-  if (!abort_sh && !first) {
+  // ---- epilogue: TMEM lane = row of C, column = [Re | Im] index.  The condition must be
+  // uniform across the CTA (tcgen05.ld is .sync.aligned): `first` is cleared by the
+  // issuing thread only, so the test uses the K range every thread sees.
+  if (!abort_sh && kb < ke) {
     const int row = warp * 32 + lane;
     float* out = part + ((size_t)blockIdx.z * na + (i0 + row)) * (2 * (size_t)nb);
     for (int c0 = 0; c0 < TN; c0 += 16) {

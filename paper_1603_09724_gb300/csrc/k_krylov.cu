@@ -353,7 +353,7 @@ cudaError_t launch_krylov_update(bool dbl, KrylovDims d, const double2* H, const
 
 // ------------------------------------------------------------------ pole combination
 template <typename T>
-__global__ void pole_combine_kernel(KrylovDims d, int P, const double2* __restrict__ w, double sign,
+__global__ void pole_combine_kernel(KrylovDims d, int P, const double2* __restrict__ w, double sign, int real_part,
                                     const cx_t<T>* __restrict__ x, cx_t<T>* __restrict__ out) {
   using C = cx_t<T>;
   const size_t total = (size_t)d.N * d.n;
@@ -365,18 +365,19 @@ __global__ void pole_combine_kernel(KrylovDims d, int P, const double2* __restri
       const C wc = mk<C>((T)(sign * wp.x), (T)(sign * wp.y));
       acc = cfma(wc, x[((size_t)p * d.N + c) * d.n + i], acc);
     }
+    if (real_part) acc.y = 0;
     out[e] = acc;
   }
 }
 
-cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w, double sign, const void* x, void* out,
-                                cudaStream_t st) {
+cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w, double sign, int real_part,
+                                const void* x, void* out, cudaStream_t st) {
   const size_t total = (size_t)d.N * d.n;
   const int blocks = (int)((total + 255) / 256 < 4864 ? (total + 255) / 256 : 4864);
   if (dbl)
-    pole_combine_kernel<double><<<blocks, 256, 0, st>>>(d, P, w, sign, (const double2*)x, (double2*)out);
+    pole_combine_kernel<double><<<blocks, 256, 0, st>>>(d, P, w, sign, real_part, (const double2*)x, (double2*)out);
   else
-    pole_combine_kernel<float><<<blocks, 256, 0, st>>>(d, P, w, sign, (const float2*)x, (float2*)out);
+    pole_combine_kernel<float><<<blocks, 256, 0, st>>>(d, P, w, sign, real_part, (const float2*)x, (float2*)out);
   return cudaGetLastError();
 }
 

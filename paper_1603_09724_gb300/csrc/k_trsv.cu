@@ -1,7 +1,8 @@
 // Device triangular solves with the multifrontal factor of the sparsifying matrix P
-// (Sec. 3.2: u~ = P^-1 Q G b, "solved by sparse direct solvers such as nested
-// dissection").  Unknowns are numbered in nested-dissection postorder; supernode s owns
-// the contiguous range [off, off + ns) and couples to the ancestor unknowns B(s).
+// (Sec. 3.2: the preconditioned vector is P^-1 Q G b, and P is factored by a sparse
+// direct method in nested-dissection order).  Unknowns are numbered in ND postorder;
+// supernode s owns the contiguous range [off, off + ns) and couples to the ancestor
+// unknowns B(s).
 //
 // With W_f = [L_SS^-1 ; L_BS L_SS^-1] and W_b = [U_SS^-1 , -U_SS^-1 U_SB] (built on the
 // host) every supernode step is one dense complex product over a tile of right-hand
@@ -9,9 +10,11 @@
 //   forward  (leaves first):  [y_S ; u_s] = W_f (b_S - sum of the update rows u_D that
 //            target S)            -- y_S kept in ND order, u_s for the ancestors
 //   backward (root first):    x_S = W_b [y_S ; x_B]   -- x_B gathered from the ancestors
-// One launch per tree height and direction.  A CTA computes RB = 64 rows of one
-// supernode's product for RT right-hand sides of one pole (system s = p * N + c), with
-// the right-hand-side block staged in shared memory and 4 x (RT/8) outputs per thread.
+// Per tree height and direction: one assembly launch (forward only) and one product
+// launch.  A product CTA computes RB = 64 rows of one supernode's product for RT
+// right-hand sides of one pole (system s = p * N + c), with the right-hand-side block
+// staged in shared memory and 4 x (RT/8) outputs per thread.  Leaves (height 0) use
+// their banded LU instead of dense W blocks (leaf_kernel).
 #include <algorithm>
 
 #include "common.cuh"
@@ -26,6 +29,59 @@ constexpr int TS_THREADS = 128;
 constexpr int RB = 64;   // rows per CTA
 constexpr int KT = 16;   // k step of the product
 
+// Forward right-hand sides of one tree height: r_S = b_S - (sum of the update rows of the
+// descendants that target S, in CSR order), for every unknown of the height and every
+// active system, written in ND order into x (x is not read before the backward sweep,
+// which overwrites every entry of an active system).  A 32 x 32 tile (unknowns x systems)
+// is transposed through shared memory so that the gather of b and the store into x run
+// unknown-fastest while the update rows are read system-fastest.
+template <typename T>
+__global__ void __launch_bounds__(256) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
+                                                       const cx_t<T>* __restrict__ b, const cx_t<T>* __restrict__ u,
+                                                       cx_t<T>* __restrict__ x, const int* __restrict__ active) {
+  using C = cx_t<T>;
+  __shared__ C tile[32][33];
+  const int i0 = blockIdx.x * 32;
+  const size_t s0 = (size_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + tx;
+    const size_t s = s0 + ty + 8 * q;
+    if (i < cnt && s < a.S && (!active || active[s])) tile[tx][ty + 8 * q] = b[s * a.n + a.perm[lunk[i]]];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ty + 8 * q;
+    const size_t s = s0 + tx;
+    if (i < cnt && s < a.S && (!active || active[s])) {
+      const int nd = lunk[i];
+      const int e0 = a.contrib_ptr[nd], e1 = a.contrib_ptr[nd + 1];
+      C acc = tile[ty + 8 * q][tx];
+      int e = e0;
+      for (; e + 4 <= e1; e += 4) {   // four independent loads in flight, subtracted in order
+        const C v0 = u[(size_t)a.contrib_idx[e] * a.S + s];
+        const C v1 = u[(size_t)a.contrib_idx[e + 1] * a.S + s];
+        const C v2 = u[(size_t)a.contrib_idx[e + 2] * a.S + s];
+        const C v3 = u[(size_t)a.contrib_idx[e + 3] * a.S + s];
+        acc = csub(csub(csub(csub(acc, v0), v1), v2), v3);
+      }
+      for (; e < e1; ++e) acc = csub(acc, u[(size_t)a.contrib_idx[e] * a.S + s]);
+      tile[ty + 8 * q][tx] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + tx;
+    const size_t s = s0 + ty + 8 * q;
+    if (i < cnt && s < a.S && (!active || active[s])) x[s * a.n + lunk[i]] = tile[tx][ty + 8 * q];
+  }
+}
+
+// Grid: (right-hand-side tiles, row blocks, poles).  The tiles of one row block are
+// adjacent in launch order, so the W rows they share are read from DRAM once.
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks,
                                                                const cx_t<T>* __restrict__ b, cx_t<T>* __restrict__ ynd,
@@ -39,49 +95,40 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
   C* Bs = reinterpret_cast<C*>(smem_raw);   // [K][RT]
   __shared__ C As[2][KT][RB + 1];                 // double-buffered W tiles
   C(*Cs)[RT + 1] = reinterpret_cast<C(*)[RT + 1]>(smem_raw);   // output staging, reuses Bs after the product
-  const int node = blocks[2 * blockIdx.x], r0 = blocks[2 * blockIdx.x + 1];
-  const int p = blockIdx.y;
-  const int c0 = blockIdx.z * RT;
+  const int node = blocks[2 * blockIdx.y], r0 = blocks[2 * blockIdx.y + 1];
+  const int p = blockIdx.z;
+  const int c0 = blockIdx.x * RT;
   const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
   const int K = FWD ? ns : ns + nb;
   const int M = FWD ? ns + nb : ns;
   const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
-  // ---- right-hand-side block
-  if (FWD) {
-    for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {   // i fastest: coalesced along a line
-      const int i = idx % ns, cc = idx / ns;
-      const int c = c0 + cc;
-      C v = mk<C>(0, 0);
-      if (c < a.N) {
-        const size_t s = (size_t)p * a.N + c;
-        if (!active || active[s]) v = b[s * a.n + a.perm[off + i]];
-      }
-      Bs[i * RT + cc] = v;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < ns * RT; idx += TS_THREADS) {   // cc fastest: u rows are [row][system]
-      const int cc = idx % RT, i = idx / RT;
-      const int c = c0 + cc;
-      if (c >= a.N) continue;
-      const size_t s = (size_t)p * a.N + c;
-      const int e0 = a.contrib_ptr[off + i], e1 = a.contrib_ptr[off + i + 1];
-      if (e0 == e1) continue;
-      C acc = Bs[i * RT + cc];
-      for (int e = e0; e < e1; ++e) acc = csub(acc, u[(size_t)a.contrib_idx[e] * a.S + s]);
-      Bs[i * RT + cc] = acc;
-    }
-  } else {
-    const int boff = a.node_boff[node];
-    for (int idx = tid; idx < K * RT; idx += TS_THREADS) {
+  (void)b;
+  // ---- right-hand-side block, i fastest (contiguous runs of one system's column); FB
+  // independent loads in flight per thread
+  constexpr int FB = 8;
+  const int boff = a.node_boff[node];
+  for (int base = tid; base < K * RT; base += FB * TS_THREADS) {
+    C v[FB];
+#pragma unroll
+    for (int q = 0; q < FB; ++q) {
+      const int idx = base + q * TS_THREADS;
       const int i = idx % K, cc = idx / K;
       const int c = c0 + cc;
-      C v = mk<C>(0, 0);
-      if (c < a.N) {
+      v[q] = mk<C>(0, 0);
+      if (idx < K * RT && c < a.N) {
         const size_t s = (size_t)p * a.N + c;
-        v = (i < ns) ? ynd[s * a.n + off + i] : x[s * a.n + a.bnat[boff + i - ns]];
+        if (FWD) {   // assembled by assemble_kernel into x, ND order
+          if (!active || active[s]) v[q] = x[s * a.n + off + i];
+        } else {
+          v[q] = (i < ns) ? ynd[s * a.n + off + i] : x[s * a.n + a.bnat[boff + i - ns]];
+        }
       }
-      Bs[i * RT + cc] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < FB; ++q) {
+      const int idx = base + q * TS_THREADS;
+      if (idx < K * RT) Bs[(idx % K) * RT + idx / K] = v[q];
     }
   }
   __syncthreads();
@@ -162,39 +209,52 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
 }
 
 
-// ---- leaves: one thread per right-hand side, the leaf's unknowns in a per-thread
-// shared-memory column; banded substitution with the leaf's own L and U (the fill of a
-// leaf stays inside the band of its x-fastest ordering), sparse couplings to the halo:
+// ---- leaves: banded substitution with the leaf's own L and U (the fill of a leaf stays
+// inside the band of its x-fastest ordering) and sparse couplings to the halo:
 //   forward:  y = L^-1 b_S,  u_s = F_BS (U^-1 y)
 //   backward: x_S = U^-1 (y_S - L^-1 (F_SB x_B))
-constexpr int LT = 64;   // right-hand sides per CTA for the leaves
+// A CTA holds LT right-hand sides of one pole and one leaf in shared memory, column cc
+// at y[i * LDY + cc], together with the leaf's factor values and index lists, staged
+// once per CTA.  Global accesses are cooperative, leaf index fastest (a warp touches
+// whole x-runs of one system's column), each one load behind an index already in shared
+// memory; only the substitutions run one thread per right-hand side, on shared memory.
+constexpr int LT = 64;        // right-hand sides per CTA for the leaves
+constexpr int LDY = LT + 1;   // padded stride: the leaf-index-fastest accesses hit distinct banks
+constexpr int LNB = 9;        // couplings per row of F_BS / F_SB (3^2 stencil)
+constexpr int LGB = 8;        // gathered loads in flight per thread
 
 template <typename T>
 __device__ __forceinline__ void band_lower(cx_t<T>* y, int ns, int bw, const cx_t<T>* Lb) {
   for (int i = 0; i < ns; ++i) {
-    cx_t<T> acc = y[i * LT];
-    const cx_t<T>* lr = Lb + (size_t)i * bw;
-    for (int t = 0; t < bw; ++t) {
-      const int j = i - 1 - t;
-      if (j < 0) break;
-      acc = csub(acc, cmul(lr[t], y[j * LT]));
-    }
-    y[i * LT] = acc;
+    cx_t<T> acc = y[i * LDY];
+    const cx_t<T>* lr = Lb + i * bw;
+    const int tn = min(bw, i);
+    for (int t = 0; t < tn; ++t) acc = csub(acc, cmul(lr[t], y[(i - 1 - t) * LDY]));
+    y[i * LDY] = acc;
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void band_upper(cx_t<T>* y, int ns, int bw, const cx_t<T>* Ub) {
   for (int i = ns - 1; i >= 0; --i) {
-    cx_t<T> acc = y[i * LT];
-    const cx_t<T>* ur = Ub + (size_t)i * (bw + 1);
-    for (int t = 1; t <= bw; ++t) {
-      const int j = i + t;
-      if (j >= ns) break;
-      acc = csub(acc, cmul(ur[t], y[j * LT]));
-    }
-    y[i * LT] = cmul(ur[0], acc);
+    cx_t<T> acc = y[i * LDY];
+    const cx_t<T>* ur = Ub + i * (bw + 1);
+    const int tn = min(bw, ns - 1 - i);
+    for (int t = 1; t <= tn; ++t) acc = csub(acc, cmul(ur[t], y[(i + t) * LDY]));
+    y[i * LDY] = cmul(ur[0], acc);
   }
+}
+
+// shared memory of one leaf CTA: y block, the leaf's values, its index lists
+__host__ __device__ inline size_t leaf_vals_count(int ns, int nb, int bw) {
+  return (size_t)ns * bw + (size_t)ns * (bw + 1) + (size_t)nb * LNB + (size_t)ns * LNB;
+}
+__host__ __device__ inline size_t leaf_idx_count(int ns, int nb) { return (size_t)ns + nb + (size_t)(ns + nb) * LNB; }
+
+template <typename T>
+size_t leaf_smem_bytes(int max_ns, int max_nb, int bw) {
+  return ((size_t)max_ns * LDY + leaf_vals_count(max_ns, max_nb, bw)) * sizeof(cx_t<T>) +
+         leaf_idx_count(max_ns, max_nb) * sizeof(int);
 }
 
 template <typename T, bool FWD>
@@ -203,54 +263,133 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
                                                   cx_t<T>* __restrict__ x, const int* __restrict__ active) {
   using C = cx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* y = reinterpret_cast<C*>(smem_raw) + threadIdx.x;   // element i at y[i * LT]
-  const int li = blockIdx.x;
+  __shared__ unsigned char live[LT];
+  const int li = blockIdx.y;
   const int node = la.nodes[li];
-  const int p = blockIdx.y;
-  const int c = blockIdx.z * LT + threadIdx.x;
-  if (c >= a.N) return;
-  const size_t s = (size_t)p * a.N + c;
-  if (active && !active[s]) return;
+  const int p = blockIdx.z;
+  const int c0 = blockIdx.x * LT;
+  const int tid = threadIdx.x;
   const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
   const int bw = la.bw;
-  constexpr int NB = 9;
-  const C* v = reinterpret_cast<const C*>(la.vals) + (size_t)p * la.leaf_size + la.voff[li];
-  const C* Lb = v;
-  const C* Ub = Lb + (size_t)ns * bw;
-  const C* Fbs = Ub + (size_t)ns * (bw + 1);
-  const C* Fsb = Fbs + (size_t)nb * NB;
+  C* ys = reinterpret_cast<C*>(smem_raw);                                    // [ns][LDY]
+  C* vs = ys + (size_t)la.max_ns * LDY;                                       // Lb | Ub | Fbs | Fsb
+  int* is = reinterpret_cast<int*>(vs + leaf_vals_count(la.max_ns, la.max_nb, bw));
+  int* iperm = is;                  // natural index of leaf unknown i
+  int* ibnat = iperm + ns;          // natural index of halo unknown j
+  int* ibs = ibnat + nb;            // F_BS columns (leaf unknowns) per halo row, -1 padded
+  int* isb = ibs + nb * LNB;        // F_SB columns (halo unknowns) per leaf row, -1 padded
+  {
+    const int c = c0 + tid;
+    live[tid] = (c < a.N) && (!active || active[(size_t)p * a.N + c]);
+  }
+  {
+    const C* v = reinterpret_cast<const C*>(la.vals) + (size_t)p * la.leaf_size + la.voff[li];
+    const int nv = (int)leaf_vals_count(ns, nb, bw);
+    for (int e = tid; e < nv; e += LT) vs[e] = v[e];
+    for (int i = tid; i < ns; i += LT) iperm[i] = a.perm[off + i];
+    if (FWD) {
+      const int* bsi = la.bs_idx + la.ioff_bs[li];
+      for (int e = tid; e < nb * LNB; e += LT) ibs[e] = bsi[e];
+    } else {
+      const int boff = a.node_boff[node];
+      const int* sbi = la.sb_idx + la.ioff_sb[li];
+      for (int j = tid; j < nb; j += LT) ibnat[j] = a.bnat[boff + j];
+      for (int e = tid; e < ns * LNB; e += LT) isb[e] = sbi[e];
+    }
+  }
+  __syncthreads();
+  const C* Lb = vs;
+  const C* Ub = Lb + ns * bw;
+  const C* Fbs = Ub + ns * (bw + 1);
+  const C* Fsb = Fbs + nb * LNB;
+  const size_t s0 = (size_t)p * a.N + c0;
+  C* y = ys + tid;
+  const bool mine = live[tid];
   if (FWD) {
-    for (int i = 0; i < ns; ++i) y[i * LT] = b[s * a.n + a.perm[off + i]];
-    band_lower<T>(y, ns, bw, Lb);
-    for (int i = 0; i < ns; ++i) ynd[s * a.n + off + i] = y[i * LT];
+    for (int base = tid; base < ns * LT; base += LGB * LT) {   // LGB independent loads in flight
+      C v[LGB];
+#pragma unroll
+      for (int q = 0; q < LGB; ++q) {
+        const int idx = base + q * LT;
+        const int i = idx % ns, cc = idx / ns;
+        if (idx < ns * LT && live[cc]) v[q] = b[(s0 + cc) * a.n + iperm[i]];
+      }
+#pragma unroll
+      for (int q = 0; q < LGB; ++q) {
+        const int idx = base + q * LT;
+        const int i = idx % ns, cc = idx / ns;
+        if (idx < ns * LT && live[cc]) ys[i * LDY + cc] = v[q];
+      }
+    }
+    __syncthreads();
+    if (mine) band_lower<T>(y, ns, bw, Lb);
+    __syncthreads();
+    for (int idx = tid; idx < ns * LT; idx += LT) {
+      const int i = idx % ns, cc = idx / ns;
+      if (live[cc]) ynd[(s0 + cc) * a.n + off + i] = ys[i * LDY + cc];
+    }
+    __syncthreads();
+    if (!mine) return;
     band_upper<T>(y, ns, bw, Ub);
     const int uoff = a.node_uoff[node];
-    const int* bsi = la.bs_idx + la.ioff_bs[li];
-    for (int j = 0; j < nb; ++j) {
+    for (int j = 0; j < nb; ++j) {   // system fastest across the CTA: coalesced update rows
       C acc = mk<C>(0, 0);
-      for (int t = 0; t < NB; ++t) {
-        const int i = bsi[j * NB + t];
-        if (i < 0) break;
-        acc = cfma(Fbs[(size_t)j * NB + t], y[i * LT], acc);
+#pragma unroll
+      for (int t = 0; t < LNB; ++t) {
+        const int i = ibs[j * LNB + t];
+        if (i >= 0) acc = cfma(Fbs[j * LNB + t], y[i * LDY], acc);
       }
-      u[(size_t)(uoff + j) * a.S + s] = acc;
+      u[(size_t)(uoff + j) * a.S + s0 + tid] = acc;
     }
   } else {
-    const int boff = a.node_boff[node];
-    const int* sbi = la.sb_idx + la.ioff_sb[li];
-    for (int i = 0; i < ns; ++i) {
-      C acc = mk<C>(0, 0);
-      for (int t = 0; t < NB; ++t) {
-        const int j = sbi[i * NB + t];
-        if (j < 0) break;
-        acc = cfma(Fsb[(size_t)i * NB + t], x[s * a.n + a.bnat[boff + j]], acc);
+    for (int base = tid; base < ns * LT; base += 4 * LT) {
+      C acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = base + q * LT;
+        const int i = idx % ns, cc = idx / ns;
+        acc[q] = mk<C>(0, 0);
+        if (idx < ns * LT && live[cc]) {
+          const C* xs = x + (s0 + cc) * a.n;
+#pragma unroll
+          for (int t = 0; t < LNB; ++t) {   // -1 entries trail: same order as a breaking loop
+            const int j = isb[i * LNB + t];
+            if (j >= 0) acc[q] = cfma(Fsb[i * LNB + t], xs[ibnat[j]], acc[q]);
+          }
+        }
       }
-      y[i * LT] = acc;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = base + q * LT;
+        const int i = idx % ns, cc = idx / ns;
+        if (idx < ns * LT && live[cc]) ys[i * LDY + cc] = acc[q];
+      }
     }
-    band_lower<T>(y, ns, bw, Lb);
-    for (int i = 0; i < ns; ++i) y[i * LT] = csub(ynd[s * a.n + off + i], y[i * LT]);
-    band_upper<T>(y, ns, bw, Ub);
-    for (int i = 0; i < ns; ++i) x[s * a.n + a.perm[off + i]] = y[i * LT];
+    __syncthreads();
+    if (mine) band_lower<T>(y, ns, bw, Lb);
+    __syncthreads();
+    for (int base = tid; base < ns * LT; base += LGB * LT) {
+      C v[LGB];
+#pragma unroll
+      for (int q = 0; q < LGB; ++q) {
+        const int idx = base + q * LT;
+        const int i = idx % ns, cc = idx / ns;
+        if (idx < ns * LT && live[cc]) v[q] = ynd[(s0 + cc) * a.n + off + i];
+      }
+#pragma unroll
+      for (int q = 0; q < LGB; ++q) {
+        const int idx = base + q * LT;
+        const int i = idx % ns, cc = idx / ns;
+        if (idx < ns * LT && live[cc]) ys[i * LDY + cc] = csub(v[q], ys[i * LDY + cc]);
+      }
+    }
+    __syncthreads();
+    if (mine) band_upper<T>(y, ns, bw, Ub);
+    __syncthreads();
+    for (int idx = tid; idx < ns * LT; idx += LT) {
+      const int i = idx % ns, cc = idx / ns;
+      if (live[cc]) x[(s0 + cc) * a.n + iperm[i]] = ys[i * LDY + cc];
+    }
   }
 }
 
@@ -275,22 +414,27 @@ static cudaError_t run_t(const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs
   }
   const int tiles = (a.N + RT - 1) / RT;
   const bool leaves = la.nleaves > 0;
-  const size_t lsm = (size_t)la.max_ns * LT * sizeof(C);
-  const dim3 lgrid(la.nleaves, P, (a.N + LT - 1) / LT);
+  const size_t lsm = leaf_smem_bytes<T>(la.max_ns, la.max_nb, la.bw);
+  const dim3 lgrid((a.N + LT - 1) / LT, la.nleaves, P);
   if (leaves) {
     leaf_kernel<T, true><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
   }
   // dynamic shared memory sized per level (the root fronts need ~100 KB)
   for (int h = leaves ? 1 : 0; h < lv.nlevels; ++h) {
     if (lv.fcount[h] == 0) continue;
-    dim3 grid(lv.fcount[h], P, tiles);
+    if (lv.ucount[h] > 0) {
+      const dim3 agrid((lv.ucount[h] + 31) / 32, (unsigned)((a.S + 31) / 32));
+      assemble_kernel<T><<<agrid, 256, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], (const C*)b, (const C*)u,
+                                                (C*)x, active);
+    }
+    dim3 grid(tiles, lv.fcount[h], P);
     const size_t sm = (size_t)std::max(lv.fkmax[h] * RT, RB * (RT + 1)) * sizeof(C);
     trsv_gemm_kernel<T, true><<<grid, TS_THREADS, sm, st>>>(a, lv.fblocks + 2 * lv.fstart[h], (const C*)b, (C*)ynd,
                                                             (C*)u, (C*)x, (const C*)factor, active);
   }
   for (int h = lv.nlevels - 1; h >= (leaves ? 1 : 0); --h) {
     if (lv.bcount[h] == 0) continue;
-    dim3 grid(lv.bcount[h], P, tiles);
+    dim3 grid(tiles, lv.bcount[h], P);
     const size_t sm = (size_t)std::max(lv.bkmax[h] * RT, RB * (RT + 1)) * sizeof(C);
     trsv_gemm_kernel<T, false><<<grid, TS_THREADS, sm, st>>>(a, lv.bblocks + 2 * lv.bstart[h], (const C*)b, (C*)ynd,
                                                              (C*)u, (C*)x, (const C*)factor, active);

@@ -50,6 +50,8 @@ cudaError_t launch_redot(bool dbl, size_t count, const void* A, const void* B, d
 size_t redot_work_bytes();
 // Convert block precision (count complex elements).
 cudaError_t launch_convert(bool to_dbl, size_t count, const void* src, void* dst, cudaStream_t st);
+// x <- Re(x) for count complex entries (imaginary parts set to zero)
+cudaError_t launch_real_part(bool dbl, size_t count, void* x, cudaStream_t st);
 
 // ---- k_small.cu: N x N algebra on one CTA (FP64)
 struct OmmScalars {
@@ -104,8 +106,9 @@ cudaError_t launch_krylov_update(bool dbl, KrylovDims d, const double2* H, const
 // *nactive = number of s with active[s] != 0
 cudaError_t launch_count_active(KrylovDims d, const int* active, int* nactive, cudaStream_t st);
 // out_c = sign * sum_p w_p x_{p N + c}
-cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w, double sign, const void* x,
-                                void* out, cudaStream_t st);
+// out = sign * sum_p w_p x_p over the P poles; real_part: out = (Re(...), 0)
+cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w, double sign, int real_part,
+                                const void* x, void* out, cudaStream_t st);
 // active[s] = 1 for all s; steps[s] = 0
 cudaError_t launch_krylov_reset(KrylovDims d, int* active, int* steps, cudaStream_t st);
 

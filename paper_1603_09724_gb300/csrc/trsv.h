@@ -31,6 +31,8 @@ struct TrsvLevels {
   const int* bblocks;         // device: same for the backward products
   std::vector<int> fstart, fcount, bstart, bcount;   // host, per height
   std::vector<int> fkmax, bkmax;                      // host, per height: shared-memory sizing
+  const int* lunk;            // device: ND indices of the unknowns of each height, concatenated
+  std::vector<int> ustart, ucount;                    // host, per height: range in lunk
 };
 
 // Leaves: banded L and U (inverted diagonal) of the leaf front and its original sparse
@@ -39,6 +41,7 @@ struct LeafArgs {
   int nleaves = 0;
   int bw = 0;
   int max_ns = 0;
+  int max_nb = 0;
   const int* nodes = nullptr;
   const long long* voff = nullptr;
   const int* ioff_bs = nullptr;

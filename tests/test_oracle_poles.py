@@ -98,3 +98,26 @@ def test_pole_expansion_equals_spectral_filter():
         np.testing.assert_allclose(Pm, ref, atol=1e-11)
     Pi = U[:, :N] @ U[:, :N].conj().T
     assert np.max(np.abs(Pm - Pi)) < 1e-6
+
+
+def test_conjugate_pairs_fold_for_real_blocks():
+    """H - sigma is real symmetric (cosine DFT with the symmetric Nyquist multiplier), so for
+    a real block R, (H - conj z)^-1 R = conj((H - z)^-1 R) and each conjugate pair of the
+    pole sum contributes 2 Re(w (H - z)^-1 R): the sum over one pole per pair, doubled, has
+    the same real part and the full sum is real."""
+    shape, L = (10, 10), 10.0
+    V = wells_2d(10, L, seed=3)
+    sig = ham.default_shift(shape, L, V)
+    H = ham.dense_h(shape, L, V, sig)
+    assert np.max(np.abs(H.imag)) < 1e-13 * np.max(np.abs(H))   # real up to the DFT's rounding
+    lam = np.linalg.eigvalsh(H)
+    N, n = 6, H.shape[0]
+    z, w = poles.poles_conformal(lam[0], lam[N - 1], lam[N], 16)
+    R = np.random.default_rng(4).standard_normal((n, 3))
+    full = sum(wj * np.linalg.solve(H - zj * np.eye(n), R) for zj, wj in zip(z, w))
+    half = sum(2 * wj * np.linalg.solve(H - zj * np.eye(n), R) for zj, wj in zip(z, w) if zj.imag > 0)
+    assert np.max(np.abs(full.imag)) < 1e-12 * np.max(np.abs(full))
+    np.testing.assert_allclose(half.real, full.real, atol=1e-12 * np.max(np.abs(full)))
+    # a planted mistake (pairs folded with conj w instead of w) fails the identity
+    bad = sum(2 * np.conj(wj) * np.linalg.solve(H - zj * np.eye(n), R) for zj, wj in zip(z, w) if zj.imag > 0)
+    assert np.max(np.abs(bad.real - full.real)) > 1e-6 * np.max(np.abs(full))

@@ -92,6 +92,14 @@ def gaussian_block(n: int, N: int, seed: int, dtype=np.complex128) -> np.ndarray
     return Z.astype(dtype)
 
 
+def gaussian_block_real(n: int, N: int, seed: int, dtype=np.complex128) -> np.ndarray:
+    """Real Gaussian n x N block, entries ~ N(0, 1/n) (unit expected column norm), in the
+    same (N, n) row-per-column layout as gaussian_block, imaginary parts zero."""
+    rng = np.random.default_rng(seed)
+    Z = np.sqrt(1.0 / n) * rng.standard_normal((N, n))
+    return Z.astype(dtype)
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     name: str
@@ -121,7 +129,11 @@ class Workload:
             return lattice_wells_3d(self.m, self.L)
         raise ValueError(self.potential)
 
-    def initial_block(self, dtype=np.complex128) -> np.ndarray:
+    def initial_block(self, dtype=np.complex128, real: bool = False) -> np.ndarray:
+        """The seeded starting block; real=True gives the real block of the same seed
+        (real orbitals, stored in the complex dtype with zero imaginary parts)."""
+        if real:
+            return gaussian_block_real(self.n, self.N, seed=1000 + self.seed, dtype=dtype)
         return gaussian_block(self.n, self.N, seed=1000 + self.seed, dtype=dtype)
 
 

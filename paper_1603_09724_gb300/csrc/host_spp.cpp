@@ -298,8 +298,10 @@ SppStructure spp_build_structure(int dim, int m, int r) {
   for (int rr = 0; rr < st.n; ++rr) st.contrib_ptr[rr + 1] = st.contrib_ptr[rr] + (int)rows[rr].size();
   st.contrib_idx.reserve(st.contrib_ptr[st.n]);
   for (int rr = 0; rr < st.n; ++rr) st.contrib_idx.insert(st.contrib_idx.end(), rows[rr].begin(), rows[rr].end());
-  // leaf data: bandwidth from the stencil couplings inside each leaf, halo couplings
-  {
+  // leaf data: bandwidth from the stencil couplings inside each leaf, halo couplings.
+  // 2D only: a cell of a 2D box couples to at most NBR = 3^2 halo cells; 3D leaves (up to
+  // 19 halo couplings per cell) keep their dense W blocks and run with the other levels.
+  if (dim == 2) {
     std::vector<int> ischild(nn, 0);
     for (int i = 0; i < nn; ++i) {
       if (bd.node_children_a[i] >= 0) ischild[i] = 1;
@@ -478,7 +480,7 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
       }
       std::vector<cd>().swap(upd[c]);
     }
-    const bool leaf = children[s].empty();
+    const bool leaf = children[s].empty() && !st.leaf_nodes.empty();   // banded leaf data (2D) is kept
     std::vector<cd> F0;
     if (leaf) F0 = F;   // original couplings of the leaf (no children: F holds only P's entries)
     // partial LU of the first ns rows / columns

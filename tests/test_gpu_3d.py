@@ -22,12 +22,17 @@ def omm():
     return m
 
 
-@pytest.mark.parametrize("m,inner,prec", [(16, "spp", 0), (16, "spp", 1), (16, "kinetic", 1), (24, "kinetic", 1)])
-def test_lattice_solve_reaches_exact_energy(omm, m, inner, prec):
-    L, N, P = 40.0, 64, 16                    # N = the s band: one state per well, gap ~6
-    V = lattice_wells_3d(m, L)
+@pytest.mark.parametrize("m,L,cells,N,inner,prec", [
+    (12, 20.0, 2, 8, "spp", 0),        # FP64 products of 16^3 exceed shared memory; 12^3 fits
+    (16, 40.0, 4, 64, "spp", 1),
+    (16, 40.0, 4, 64, "kinetic", 1),
+    (24, 40.0, 4, 64, "kinetic", 1)])
+def test_lattice_solve_reaches_exact_energy(omm, m, L, cells, N, inner, prec):
+    """N = the s band (one state per well), separated by a gap of ~5-6."""
+    P = 16
+    V = lattice_wells_3d(m, L, cells=cells)
     sig = ham.default_shift((m,) * 3, L, V)
-    lam = spectrum.lowest_eigs_bloch((m,) * 3, L, V, sig, 4, N + 1)
+    lam = spectrum.lowest_eigs_bloch((m,) * 3, L, V, sig, cells, N + 1)
     z, w = opoles.poles_conformal(lam[0], lam[N - 1], lam[N], P)
     p = omm.default_params(precision=prec, maxit=40, tol=1e-13 if prec == 0 else 1e-10, real_orbitals=1,
                            inner=omm.OMM_INNER_SPARSIFY if inner == "spp" else omm.OMM_INNER_KINETIC)

@@ -57,11 +57,13 @@ def test_apply_h_matches_oracle(omm, dim, m, L, prec):
         assert err < (FP64_RTOL if prec == 0 else FP32_RTOL), (dim, m, prec, err)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec,tensor", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("na,nb,n", [(3, 5, 256), (16, 64, 1024), (40, 33, 4096), (128, 512, 16384)])
-def test_gram_matches_definition(omm, prec, na, nb, n):
+def test_gram_matches_definition(omm, prec, tensor, na, nb, n):
+    """CUDA-core Gram (FP32 products, FP64 sums) and the tcgen05 Gram (TF32 x 3 split with
+    FP32 accumulation in tensor memory, FP64 split-K sum), against A^H B in FP64."""
     m = int(round(np.sqrt(n)))
-    s, _ = make(omm, 2, m, 10.0, 2, prec)
+    s, _ = make(omm, 2, m, 10.0, 2, prec, gram_tensor=tensor)
     dt = torch.complex128 if prec == 0 else torch.complex64
     A = gaussian_block(n, na, seed=1)
     B = gaussian_block(n, nb, seed=2)
@@ -71,7 +73,7 @@ def test_gram_matches_definition(omm, prec, na, nb, n):
     Ar, Br = to_host(Ad), to_host(Bd)
     ref = Ar.conj() @ Br.T
     err = rel_err(Cg, ref)
-    assert err < (1e-13 if prec == 0 else 2e-6), err
+    assert err < (1e-13 if prec == 0 else (3e-5 if tensor else 2e-6)), err
 
 
 @pytest.mark.parametrize("prec", [0, 1])

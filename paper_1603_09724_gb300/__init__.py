@@ -78,7 +78,7 @@ _SIGS = {
     "omm_profile_class_name": (C.c_char_p, [C.c_int]),
     "omm_gram_noalloc": (C.c_int, [C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_size_t, _vp, _vp]),
 }
-PROFILE_CLASSES = ("happly", "greenq", "trsv", "orth", "gram", "block_update", "vector", "small")
+PROFILE_CLASSES = ("happly", "greenq", "trsv_levels", "orth", "gram", "block_update", "vector", "small", "trsv_leaf")
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
     _f.restype = _res

@@ -42,8 +42,9 @@ void omm_internal_set_cuda_error(cudaError_t e, const char* what, const char* fi
 
 static void omm_internal_set_message(const char* msg) { g_last_error = msg; }
 
-enum ProfClass { PC_HAPPLY = 0, PC_GREENQ, PC_TRSV, PC_ORTH, PC_GRAM, PC_BLOCKUPD, PC_VEC, PC_SMALL, PC_NCLS };
-const char* const kProfNames[PC_NCLS] = {"happly", "greenq", "trsv", "orth", "gram", "block_update", "vector", "small"};
+enum ProfClass { PC_HAPPLY = 0, PC_GREENQ, PC_TRSV, PC_ORTH, PC_GRAM, PC_BLOCKUPD, PC_VEC, PC_SMALL, PC_TRSV_LEAF, PC_NCLS };
+const char* const kProfNames[PC_NCLS] = {"happly", "greenq", "trsv_levels", "orth", "gram", "block_update", "vector",
+                                         "small", "trsv_leaf"};
 
 struct Prof {
   bool on = false;
@@ -163,6 +164,10 @@ struct omm_ctx {
   void* leafvals = nullptr;     // P * leaf_size complex
   int* d_bblocks = nullptr;
   int* d_lunk = nullptr;                    // unknowns of each tree height (ND indices)
+  // algorithmic complex elements of the triangular-solve phases: per system and per pole
+  double tb_leaf_fwd_sys = 0, tb_leaf_bwd_sys = 0, tb_leaf_pole = 0, tb_lvl_sys = 0, tb_lvl_pole = 0;
+  long long nact_last = -1;   // systems active after the last count (-1: unknown); algorithmic bytes
+                              // of masked launches count these only
   std::vector<int> lunk_start, lunk_count;
   size_t trsv_smem = 0;
   int last_gmres_max = 0;
@@ -291,6 +296,11 @@ bool radix_ok(int m) {
 
 omm_status ensure_fft_tmp(omm_ctx* h, size_t ncols, bool dbl);
 
+// columns a masked launch touches (for its algorithmic bytes): the active count when known
+double live_cols(const omm_ctx* h, double ncols, const int* active) {
+  return (active && h->nact_last >= 0) ? std::min(ncols, (double)h->nact_last) : ncols;
+}
+
 // H0 X (shift 0) or (H0 - s_g) X for ncols columns; fused single-CTA kernel when the grid
 // fits shared memory, else the multi-pass kernels
 omm_status happly(omm_ctx* h, const void* X, void* Y, int ncols, const double2* shifts, int cpg, const int* active,
@@ -299,7 +309,7 @@ omm_status happly(omm_ctx* h, const void* X, void* Y, int ncols, const double2* 
   const void* V = fp64 ? h->V64 : h->V;
   const void* tw = fp64 ? h->tw64 : h->tw;
   const double kn = h->kin / (double)h->n;
-  const double bytes = (2.0 * ncols * (dbl ? 16 : 8) + (dbl ? 8 : 4)) * (double)h->n;
+  const double bytes = (2.0 * live_cols(h, ncols, active) * (dbl ? 16 : 8) + (dbl ? 8 : 4)) * (double)h->n;
   if (fused_fft_supported(h->dim, h->m, dbl)) {
     PROF(PC_HAPPLY, bytes, 1,
          cuda_status(launch_happly(dbl, h->dim, h->m, X, Y, ncols, V, shifts, cpg, tw, kn, active, h->st), "happly"));
@@ -316,7 +326,7 @@ omm_status greenq(omm_ctx* h, const void* B, void* Out, int ncols, int nq, int c
                   const void* ghat = nullptr, const void* q = nullptr) {
   if (!ghat) ghat = h->ghat;
   if (!q) q = h->qd;
-  const double bytes = (2.0 * ncols + (double)((ncols + cpg - 1) / cpg)) * h->csz * (double)h->n;
+  const double bytes = (2.0 * live_cols(h, ncols, active) + (double)((ncols + cpg - 1) / cpg)) * h->csz * (double)h->n;
   if (fused_fft_supported(h->dim, h->m, h->dbl)) {
     PROF(PC_GREENQ, bytes, 1,
          cuda_status(launch_greenq(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, h->st),
@@ -471,15 +481,23 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   OMM_TRY(greenq(h, Vk, tmp, (int)S, h->nq, Ncols, active));
   TrsvArgs a = trsv_args(h, Ncols, S);
   TrsvLevels lv = trsv_levels(h);
-  const double bytes = ((double)P * h->spp.factor_size + (4.0 * h->n + 2.0 * h->spp.urows) * (double)S) * h->csz;
+  const LeafArgs la = leaf_args(h, 0);
+  const bool has_leaves = la.nleaves > 0;
+  const double cs = (double)h->csz;
+  const double Se = live_cols(h, (double)S, active);
   int nk = 0;
-  const bool has_leaves = !h->spp.leaf_nodes.empty();
-  for (int l = 0; l < lv.nlevels; ++l)   // per height: (assembly +) product forward, product backward
-    nk += (lv.fcount[l] > 0) * (1 + ((l > 0 || !has_leaves) && lv.ucount[l] > 0)) + (lv.bcount[l] > 0);
-  PROF(PC_TRSV, bytes, nk,
-       cuda_status(launch_spp_solve(h->dbl, a, lv, leaf_args(h, 0), P, tmp, h->ynd, h->ubuf, Z, h->factor, active,
-                                    h->trsv_smem, h->st),
-                   "spp"));
+  for (int l = has_leaves ? 1 : 0; l < lv.nlevels; ++l)   // per height: (assembly +) product forward, product backward
+    nk += (lv.fcount[l] > 0) * (1 + (lv.ucount[l] > 0)) + (lv.bcount[l] > 0);
+  auto spp = [&](int phases) {
+    return cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, P, tmp, h->ynd, h->ubuf, Z, h->factor, active,
+                                        h->trsv_smem, h->st),
+                       "spp");
+  };
+  if (has_leaves)
+    PROF(PC_TRSV_LEAF, (h->tb_leaf_fwd_sys * Se + h->tb_leaf_pole * P) * cs, 1, spp(SPP_LEAF_FWD));
+  PROF(PC_TRSV, (h->tb_lvl_sys * Se + h->tb_lvl_pole * P) * cs, nk, spp(SPP_LEVELS_FWD | SPP_LEVELS_BWD));
+  if (has_leaves)
+    PROF(PC_TRSV_LEAF, (h->tb_leaf_bwd_sys * Se + h->tb_leaf_pole * P) * cs, 1, spp(SPP_LEAF_BWD));
   return OMM_OK;
 }
 
@@ -487,6 +505,7 @@ omm_status read_nactive(omm_ctx* h, int* out) {
   OMM_TRY(cuda_status(cudaMemcpyAsync(h->nact_h, h->nact_d, sizeof(int), cudaMemcpyDeviceToHost, h->st), "nact"));
   OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "nact sync"));
   *out = *h->nact_h;
+  h->nact_last = *out;
   return OMM_OK;
 }
 
@@ -505,6 +524,7 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
   const int fixed = h->prm.gmres_fixed;
   OMM_TRY(cuda_status(cudaMemsetAsync(h->itot, 0, sizeof(int) * d.S, h->st), "memset"));
   for (int cyc = 0; cyc < h->prm.gmres_cycles; ++cyc) {
+    h->nact_last = -1;   // every system until the cycle start has been counted
     OMM_TRY(cuda_status(cudaMemsetAsync(h->steps, 0, sizeof(int) * d.S, h->st), "memset"));
     if (cyc == 0) {
       OMM_TRY(happly(h, R, h->wv, N, h->zero_shift, N, nullptr));
@@ -519,17 +539,21 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
                                              fixed, h->st),
                        "restart"));
     }
+    double cyc_cols = d.S;   // systems the cycle works on (for the update's bytes)
     if (!fixed) {
       // count active systems after the cycle start
       PROF(PC_SMALL, 0, 1, cuda_status(launch_count_active(d, h->active, h->nact_d, h->st), "count"));
       int na = 0;
       OMM_TRY(read_nactive(h, &na));
       if (na == 0) break;
+      cyc_cols = na;
     }
+    int steps_run = 0;
     for (int k = 0; k < d.m; ++k) {
+      ++steps_run;
       OMM_TRY(inner_apply(h, P, N, Vk(k), Zk(k), h->active, h->tv));
       OMM_TRY(happly(h, Zk(k), h->wv, d.S, h->shifts, N, h->active));
-      PROF(PC_ORTH, (2.0 * (k + 1) + 3.0) * d.S * h->n * h->csz, 1,
+      PROF(PC_ORTH, (2.0 * (k + 1) + 3.0) * live_cols(h, d.S, h->active) * h->n * h->csz, 1,
            cuda_status(launch_krylov_orth(h->dbl, d, k, h->Vb, h->wv, h->Hh, h->active, h->st), "orth"));
       OMM_TRY(cuda_status(cudaMemsetAsync(h->nact_d, 0, sizeof(int), h->st), "memset"));
       PROF(PC_SMALL, 0, 1,
@@ -542,7 +566,7 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
         if (na == 0) break;
       }
     }
-    PROF(PC_VEC, (d.m + 2.0) * d.S * h->n * h->csz, 2,
+    PROF(PC_VEC, (steps_run + 2.0) * cyc_cols * h->n * h->csz, 2,
          cuda_status(launch_krylov_update(h->dbl, d, h->Hh, h->gv, h->steps, h->yv, h->Zb, h->xs, h->itot, h->st),
                      "update"));
   }
@@ -755,7 +779,9 @@ omm_status build_spp(omm_ctx* h) {
   if (!h->spp_built) {
     h->spp = spp_build_structure(h->dim, h->m, h->prm.stencil_radius);
     const SppStructure& s = h->spp;
-    h->trsv_smem = trsv_smem_bytes(h->dbl, s.max_ns, s.max_nb);
+    int kmax = 0;   // largest right-hand-side block of any product (per-level sizing)
+    for (size_t lh = 0; lh < s.fkmax.size(); ++lh) kmax = std::max(kmax, std::max(s.fkmax[lh], s.bkmax[lh]));
+    h->trsv_smem = trsv_smem_bytes(h->dbl, kmax, 0);
     if (h->trsv_smem > 220 * 1024) return OMM_EUNSUPPORTED;
     std::vector<int> ns, nb, off, boff, uoff;
     std::vector<long long> wf, wb;
@@ -776,6 +802,24 @@ omm_status build_spp(omm_ctx* h) {
     OMM_TRY(upload_vec(h, &h->d_cidx, s.contrib_idx));
     OMM_TRY(upload_vec(h, &h->d_fblocks, s.fblocks));
     OMM_TRY(upload_vec(h, &h->d_bblocks, s.bblocks));
+    {
+      // byte model of the triangular-solve phases (complex elements)
+      double nl = 0, ubl = 0, ubs = 0, flv = 0;
+      std::vector<char> isleaf(s.nodes.size(), 0);
+      for (int id : s.leaf_nodes) isleaf[id] = 1;
+      for (size_t id = 0; id < s.nodes.size(); ++id) {
+        const SppNode& nd = s.nodes[id];
+        if (isleaf[id]) { nl += nd.ns; ubl += nd.nb; }
+        else { ubs += nd.nb; flv += 2.0 * (double)(nd.ns + nd.nb) * nd.ns; }
+      }
+      const double nsep = (double)s.n - nl;
+      h->tb_leaf_fwd_sys = 2 * nl + ubl;              // b in, y out, update rows out
+      h->tb_leaf_bwd_sys = ubl + 2 * nl;              // halo x in, y in, x out
+      h->tb_leaf_pole = (double)s.leaf_size;
+      h->tb_lvl_sys = nsep + (double)s.contrib_idx.size() + 2 * nsep + nsep + ubs   // forward
+                      + nsep + ubs + nsep;                                          // backward
+      h->tb_lvl_pole = flv;
+    }
     {
       std::vector<int> lunk;
       h->lunk_start.assign(s.levels.size(), 0);
@@ -1208,7 +1252,7 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
   TrsvArgs a = trsv_args(h, ncols, (size_t)ncols);
   TrsvLevels lv = trsv_levels(h);
   const void* f = (char*)h->factor + (size_t)pole * h->spp.factor_size * h->csz;
-  OMM_TRY(cuda_status(launch_spp_solve(h->dbl, a, lv, leaf_args(h, pole), 1, h->tv, h->ynd, h->ubuf, U, f, nullptr,
+  OMM_TRY(cuda_status(launch_spp_solve(SPP_ALL, h->dbl, a, lv, leaf_args(h, pole), 1, h->tv, h->ynd, h->ubuf, U, f, nullptr,
                                        h->trsv_smem, h->st),
                       "spp"));
   return cuda_status(cudaStreamSynchronize(h->st), "sync");

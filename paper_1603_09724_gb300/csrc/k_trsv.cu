@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
   }
 }
 
+// Shared memory of the largest product launch: K = max_ns + max_nb right-hand-side rows.
 size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb) {
   const int RT = dbl ? TrsvCfg<double>::RT : TrsvCfg<float>::RT;
   const size_t cs = dbl ? sizeof(double2) : sizeof(float2);
@@ -401,7 +402,7 @@ size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb) {
 }
 
 template <typename T>
-static cudaError_t run_t(const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P, const void* b, void* ynd,
+static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P, const void* b, void* ynd,
                          void* u, void* x, const void* factor, const int* active, size_t smem_total,
                          cudaStream_t st) {
   using C = cx_t<T>;
@@ -416,11 +417,11 @@ static cudaError_t run_t(const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs
   const bool leaves = la.nleaves > 0;
   const size_t lsm = leaf_smem_bytes<T>(la.max_ns, la.max_nb, la.bw);
   const dim3 lgrid((a.N + LT - 1) / LT, la.nleaves, P);
-  if (leaves) {
+  if (leaves && (phases & SPP_LEAF_FWD)) {
     leaf_kernel<T, true><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
   }
   // dynamic shared memory sized per level (the root fronts need ~100 KB)
-  for (int h = leaves ? 1 : 0; h < lv.nlevels; ++h) {
+  for (int h = leaves ? 1 : 0; h < lv.nlevels && (phases & SPP_LEVELS_FWD); ++h) {
     if (lv.fcount[h] == 0) continue;
     if (lv.ucount[h] > 0) {
       const dim3 agrid((lv.ucount[h] + 31) / 32, (unsigned)((a.S + 31) / 32));
@@ -432,22 +433,23 @@ static cudaError_t run_t(const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs
     trsv_gemm_kernel<T, true><<<grid, TS_THREADS, sm, st>>>(a, lv.fblocks + 2 * lv.fstart[h], (const C*)b, (C*)ynd,
                                                             (C*)u, (C*)x, (const C*)factor, active);
   }
-  for (int h = lv.nlevels - 1; h >= (leaves ? 1 : 0); --h) {
+  for (int h = lv.nlevels - 1; h >= (leaves ? 1 : 0) && (phases & SPP_LEVELS_BWD); --h) {
     if (lv.bcount[h] == 0) continue;
     dim3 grid(tiles, lv.bcount[h], P);
     const size_t sm = (size_t)std::max(lv.bkmax[h] * RT, RB * (RT + 1)) * sizeof(C);
     trsv_gemm_kernel<T, false><<<grid, TS_THREADS, sm, st>>>(a, lv.bblocks + 2 * lv.bstart[h], (const C*)b, (C*)ynd,
                                                              (C*)u, (C*)x, (const C*)factor, active);
   }
-  if (leaves) leaf_kernel<T, false><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
+  if (leaves && (phases & SPP_LEAF_BWD))
+    leaf_kernel<T, false><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spp_solve(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
+cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
                              const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
                              size_t smem, cudaStream_t st) {
-  if (dbl) return run_t<double>(a, lv, la, P, b, ynd, u, x, factor, active, smem, st);
-  return run_t<float>(a, lv, la, P, b, ynd, u, x, factor, active, smem, st);
+  if (dbl) return run_t<double>(phases, a, lv, la, P, b, ynd, u, x, factor, active, smem, st);
+  return run_t<float>(phases, a, lv, la, P, b, ynd, u, x, factor, active, smem, st);
 }
 
 }  // namespace omm

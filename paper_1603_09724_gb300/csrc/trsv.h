@@ -54,7 +54,10 @@ struct LeafArgs {
 
 size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb);
 // b (natural, S systems) -> x (natural); ynd, u work buffers.  factor: P poles' blocks.
-cudaError_t launch_spp_solve(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
+// phases: bit 0 leaves forward, bit 1 levels forward, bit 2 levels backward, bit 3 leaves
+// backward (SPP_ALL = 15); the phases must run in that order.
+constexpr int SPP_LEAF_FWD = 1, SPP_LEVELS_FWD = 2, SPP_LEVELS_BWD = 4, SPP_LEAF_BWD = 8, SPP_ALL = 15;
+cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
                              const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
                              size_t smem, cudaStream_t st);
 

@@ -26,7 +26,7 @@ def omm():
     (12, 20.0, 2, 8, "spp", 0),        # FP64 products of 16^3 exceed shared memory; 12^3 fits
     (16, 40.0, 4, 64, "spp", 1),
     (16, 40.0, 4, 64, "kinetic", 1),
-    (24, 40.0, 4, 64, "kinetic", 1)])
+    (32, 40.0, 4, 64, "kinetic", 1)])
 def test_lattice_solve_reaches_exact_energy(omm, m, L, cells, N, inner, prec):
     """N = the s band (one state per well), separated by a gap of ~5-6."""
     P = 16

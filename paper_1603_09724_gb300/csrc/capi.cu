@@ -316,7 +316,7 @@ omm_status happly(omm_ctx* h, const void* X, void* Y, int ncols, const double2* 
     return OMM_OK;
   }
   OMM_TRY(ensure_fft_tmp(h, ncols, dbl));
-  PROF(PC_HAPPLY, bytes, h->dim == 3 ? 5 : 3,
+  PROF(PC_HAPPLY, bytes, big_fft_launches(h->dim, h->m, dbl, false),
        cuda_status(launch_happly_big(dbl, h->dim, h->m, X, Y, ncols, V, shifts, cpg, tw, kn, active, h->fft_tmp, h->st),
                    "happly"));
   return OMM_OK;
@@ -334,7 +334,7 @@ omm_status greenq(omm_ctx* h, const void* B, void* Out, int ncols, int nq, int c
     return OMM_OK;
   }
   OMM_TRY(ensure_fft_tmp(h, ncols, h->dbl));
-  PROF(PC_GREENQ, bytes, h->dim == 3 ? 6 : 4,
+  PROF(PC_GREENQ, bytes, big_fft_launches(h->dim, h->m, h->dbl, true),
        cuda_status(
            launch_greenq_big(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, h->fft_tmp, h->st),
            "greenq"));

@@ -129,6 +129,70 @@ __global__ void __launch_bounds__(BT) lpass_kernel(cx_t<T>* __restrict__ buf, si
   }
 }
 
+// ---- xy slab pass (3D): one CTA transforms a whole z-slab (M x M) along x and y in shared
+// memory, so a 3D transform is two kernels (xy slabs, z pencils) instead of three.
+// mode 0: forward, in -> out.  mode 1: inverse and finish the H-apply:
+// out = F_xy^-1 in + (V - s) X.  mode 2: inverse only.  in and out may alias.
+template <typename T, int M>
+struct SlabCfg {
+  using LY = fft::Layout<M, M, 1>;
+  static constexpr size_t smem = sizeof(cx_t<T>) * (LY::SIZE + M);
+};
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(BT) xyslab_kernel(const cx_t<T>* in, cx_t<T>* out, size_t n,
+                                                    const cx_t<T>* __restrict__ tw, const T* __restrict__ V,
+                                                    const cx_t<T>* __restrict__ X, const double2* __restrict__ shifts,
+                                                    int cpg, const int* __restrict__ active) {
+  using C = cx_t<T>;
+  using LY = typename SlabCfg<T, M>::LY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  C* t = s + LY::SIZE;
+  const int col = blockIdx.x / M, z = blockIdx.x % M;
+  if (active && !active[col]) return;
+  const size_t base = (size_t)col * n + (size_t)z * M * M;
+  for (int i = threadIdx.x; i < M; i += BT) t[i] = tw[i];
+  for (int i = threadIdx.x; i < M * M; i += BT) s[LY::at_flat(i)] = in[base + i];
+  __syncthreads();
+  if (MODE == 0) fft::transform<-1, LY, 1, BT>(s, t, t, t);
+  else fft::transform<+1, LY, 1, BT>(s, t, t, t);
+  if (MODE != 1) {
+    for (int i = threadIdx.x; i < M * M; i += BT) out[base + i] = s[LY::at_flat(i)];
+  } else {
+    const double2 sh = shifts[col / cpg];
+    const T sr = (T)sh.x, si = (T)sh.y;
+    const size_t off = (size_t)z * M * M;
+    for (int i = threadIdx.x; i < M * M; i += BT) {
+      const C xi = X[base + i];
+      const T vr = V[off + i] - sr;
+      C r = s[LY::at_flat(i)];
+      r.x += vr * xi.x + si * xi.y;
+      r.y += vr * xi.y - si * xi.x;
+      out[base + i] = r;
+    }
+  }
+}
+
+// slabs up to this many bytes of shared memory take the two-kernel 3D path
+constexpr size_t kSlabSmemMax = 100 * 1024;
+
+template <typename T, int M>
+static bool slab_ok(int dim) {
+  return dim == 3 && SlabCfg<T, M>::smem <= kSlabSmemMax;
+}
+
+template <typename T, int M, int MODE>
+static cudaError_t launch_xyslab(const cx_t<T>* in, cx_t<T>* out, size_t n, int ncols, const cx_t<T>* tw,
+                                 const T* V, const cx_t<T>* X, const double2* shifts, int cpg, const int* active,
+                                 cudaStream_t st) {
+  auto k = xyslab_kernel<T, M, MODE>;
+  cudaError_t e = raise_smem_limit((const void*)k);
+  if (e != cudaSuccess) return e;
+  k<<<ncols * M, BT, SlabCfg<T, M>::smem, st>>>(in, out, n, tw, V, X, shifts, cpg, active);
+  return cudaGetLastError();
+}
+
 // ---- Q stencil on a natural-order grid function: out[j] = sum_t q_t in[j + o_t]
 template <typename T>
 __global__ void stencil_kernel(const cx_t<T>* __restrict__ in, cx_t<T>* __restrict__ out, int dim, int m, size_t n,
@@ -166,6 +230,12 @@ static cudaError_t happly_big_t(int dim, const void* X, void* Y, int ncols, cons
   const C* x = (const C*)X;
   C* w = (C*)tmp;
   const C* t = (const C*)tw;
+  if (slab_ok<T, M>(dim)) {   // xy slabs forward, z pencils forward-multiply-inverse, xy slabs inverse + V
+    cudaError_t e = launch_xyslab<T, M, 0>(x, w, n, ncols, t, nullptr, nullptr, nullptr, 1, active, st);
+    if (e != cudaSuccess) return e;
+    lpass_kernel<T, M, 3, 2, 2><<<ncols * lt, BT, 0, st>>>(w, n, t, kin_over_n, nullptr, 1, active, lt);
+    return launch_xyslab<T, M, 1>(w, (C*)Y, n, ncols, t, (const T*)V, x, shifts, cpg, active, st);
+  }
   xpass_kernel<T, M, 0><<<ncols * xt, BT, 0, st>>>(x, w, n, t, nullptr, nullptr, nullptr, 1, active, xt);
   if (dim == 2) {
     lpass_kernel<T, M, 2, 1, 2><<<ncols * lt, BT, 0, st>>>(w, n, t, kin_over_n, nullptr, 1, active, lt);
@@ -188,6 +258,16 @@ static cudaError_t greenq_big_t(int dim, const void* B, void* Out, int ncols, co
   C* w = (C*)tmp;
   const C* t = (const C*)tw;
   const C* gh = (const C*)ghat;
+  const int sb = (int)((n + 255) / 256 < 256 ? (n + 255) / 256 : 256);
+  if (slab_ok<T, M>(dim)) {
+    cudaError_t e = launch_xyslab<T, M, 0>((const C*)B, w, n, ncols, t, nullptr, nullptr, nullptr, 1, active, st);
+    if (e != cudaSuccess) return e;
+    lpass_kernel<T, M, 3, 2, 3><<<ncols * lt, BT, 0, st>>>(w, n, t, 0.0, gh, cpg, active, lt);
+    e = launch_xyslab<T, M, 2>(w, w, n, ncols, t, nullptr, nullptr, nullptr, 1, active, st);
+    if (e != cudaSuccess) return e;
+    stencil_kernel<T><<<dim3(sb, ncols), 256, 0, st>>>(w, (C*)Out, dim, M, n, (const C*)q, nq, cpg, active);
+    return cudaGetLastError();
+  }
   xpass_kernel<T, M, 0><<<ncols * xt, BT, 0, st>>>((const C*)B, w, n, t, nullptr, nullptr, nullptr, 1, active, xt);
   if (dim == 2) {
     lpass_kernel<T, M, 2, 1, 3><<<ncols * lt, BT, 0, st>>>(w, n, t, 0.0, gh, cpg, active, lt);
@@ -197,9 +277,16 @@ static cudaError_t greenq_big_t(int dim, const void* B, void* Out, int ncols, co
     lpass_kernel<T, M, 3, 1, 1><<<ncols * lt, BT, 0, st>>>(w, n, t, 0.0, gh, cpg, active, lt);
   }
   xpass_kernel<T, M, 2><<<ncols * xt, BT, 0, st>>>(w, w, n, t, nullptr, nullptr, nullptr, 1, active, xt);
-  const int sb = (int)((n + 255) / 256 < 256 ? (n + 255) / 256 : 256);
   stencil_kernel<T><<<dim3(sb, ncols), 256, 0, st>>>(w, (C*)Out, dim, M, n, (const C*)q, nq, cpg, active);
   return cudaGetLastError();
+}
+
+// kernels one call launches (for the launch counts of the profiler)
+int big_fft_launches(int dim, int m, bool dbl, bool greenq) {
+  size_t smem = (dbl ? sizeof(double2) : sizeof(float2)) * ((size_t)(m + 1) * m + m);
+  const bool slab = dim == 3 && smem <= kSlabSmemMax;
+  if (slab) return greenq ? 4 : 3;
+  return (dim == 3 ? 5 : 3) + (greenq ? 1 : 0);
 }
 
 bool big_fft_supported(int dim, int m) {

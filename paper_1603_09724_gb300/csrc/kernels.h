@@ -16,6 +16,8 @@ cudaError_t launch_greenq(bool dbl, int dim, int m, const void* B, void* Out, in
 
 // ---- k_fft_big.cu: multi-pass (per-axis) kernels for large grids; tmp: ncols * n complex
 bool big_fft_supported(int dim, int m);
+// kernels one multi-pass H-apply (greenq = false) or Green apply (true) launches
+int big_fft_launches(int dim, int m, bool dbl, bool greenq);
 cudaError_t launch_happly_big(bool dbl, int dim, int m, const void* X, void* Y, int ncols, const void* V,
                               const double2* shifts, int cols_per_group, const void* tw, double kin_over_n,
                               const int* active, void* tmp, cudaStream_t st);

@@ -25,40 +25,44 @@ namespace omm {
 template <typename T> struct TrsvCfg;
 template <> struct TrsvCfg<float> { static constexpr int RT = 32; };
 template <> struct TrsvCfg<double> { static constexpr int RT = 16; };
-constexpr int TS_THREADS = 128;
 constexpr int RB = 64;   // rows per CTA
 constexpr int KT = 16;   // k step of the product
 
 // Forward right-hand sides of one tree height: r_S = b_S - (sum of the update rows of the
 // descendants that target S, in CSR order), for every unknown of the height and every
 // active system, written in ND order into x (x is not read before the backward sweep,
-// which overwrites every entry of an active system).  A 32 x 32 tile (unknowns x systems)
-// is transposed through shared memory so that the gather of b and the store into x run
-// unknown-fastest while the update rows are read system-fastest.
+// which overwrites every entry of an active system).  An AS_I x 32 tile (unknowns x
+// systems, one element per thread) is transposed through shared memory so that the gather
+// of b and the store into x run unknown-fastest while the update rows are read
+// system-fastest.  Small tiles: the top heights have few unknowns, and each element waits
+// on a chain of loads, so the grid needs many CTAs.
+constexpr int AS_I = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(256) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
-                                                       const cx_t<T>* __restrict__ b, const cx_t<T>* __restrict__ u,
-                                                       cx_t<T>* __restrict__ x, const int* __restrict__ active) {
+__global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
+                                                              const cx_t<T>* __restrict__ b,
+                                                              const cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
+                                                              const int* __restrict__ active) {
   using C = cx_t<T>;
-  __shared__ C tile[32][33];
-  const int i0 = blockIdx.x * 32;
+  __shared__ C tile[AS_I][33];
+  const int i0 = blockIdx.x * AS_I;
   const size_t s0 = (size_t)blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = i0 + tx;
-    const size_t s = s0 + ty + 8 * q;
-    if (i < cnt && s < a.S && (!active || active[s])) tile[tx][ty + 8 * q] = b[s * a.n + a.perm[lunk[i]]];
+  const int t = threadIdx.x;
+  {
+    const int ii = t % AS_I, ss = t / AS_I;   // unknown fastest
+    const int i = i0 + ii;
+    const size_t s = s0 + ss;
+    if (i < cnt && s < a.S && (!active || active[s])) tile[ii][ss] = b[s * a.n + a.perm[lunk[i]]];
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = i0 + ty + 8 * q;
-    const size_t s = s0 + tx;
+  {
+    const int ss = t % 32, ii = t / 32;       // system fastest
+    const int i = i0 + ii;
+    const size_t s = s0 + ss;
     if (i < cnt && s < a.S && (!active || active[s])) {
       const int nd = lunk[i];
       const int e0 = a.contrib_ptr[nd], e1 = a.contrib_ptr[nd + 1];
-      C acc = tile[ty + 8 * q][tx];
+      C acc = tile[ii][ss];
       int e = e0;
       for (; e + 4 <= e1; e += 4) {   // four independent loads in flight, subtracted in order
         const C v0 = u[(size_t)a.contrib_idx[e] * a.S + s];
@@ -68,39 +72,45 @@ __global__ void __launch_bounds__(256) assemble_kernel(TrsvArgs a, const int* __
         acc = csub(csub(csub(csub(acc, v0), v1), v2), v3);
       }
       for (; e < e1; ++e) acc = csub(acc, u[(size_t)a.contrib_idx[e] * a.S + s]);
-      tile[ty + 8 * q][tx] = acc;
+      tile[ii][ss] = acc;
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = i0 + tx;
-    const size_t s = s0 + ty + 8 * q;
-    if (i < cnt && s < a.S && (!active || active[s])) x[s * a.n + lunk[i]] = tile[tx][ty + 8 * q];
+  {
+    const int ii = t % AS_I, ss = t / AS_I;
+    const int i = i0 + ii;
+    const size_t s = s0 + ss;
+    if (i < cnt && s < a.S && (!active || active[s])) x[s * a.n + lunk[i]] = tile[ii][ss];
   }
 }
 
 // Grid: (right-hand-side tiles, row blocks, poles).  The tiles of one row block are
 // adjacent in launch order, so the W rows they share are read from DRAM once.
-template <typename T, bool FWD>
-__global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks,
+// RBV rows x RTV right-hand sides per CTA with NTH threads, 4 rows x TC columns per thread.
+// The host's row blocks are 64 rows; a smaller RBV splits each into `split` CTAs (grid.y):
+// for the top of the tree, where 64-row blocks leave most SMs idle, and for thin nodes.
+template <typename T, bool FWD, int RBV, int RTV, int NTH>
+__global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks,
                                                                const cx_t<T>* __restrict__ b, cx_t<T>* __restrict__ ynd,
                                                                cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
                                                                const cx_t<T>* __restrict__ factor,
-                                                               const int* __restrict__ active) {
+                                                               const int* __restrict__ active, int split) {
   using C = cx_t<T>;
-  constexpr int RT = TrsvCfg<T>::RT;
-  constexpr int TC = RT / 8;   // columns per thread
+  constexpr int RT = RTV;
+  constexpr int TC = RTV * (RBV / 4) / NTH;   // columns per thread
+  constexpr int CG = RTV / TC;                // column groups
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Bs = reinterpret_cast<C*>(smem_raw);   // [K][RT]
-  __shared__ C As[2][KT][RB + 1];                 // double-buffered W tiles
+  __shared__ C As[2][KT][RBV + 1];                 // double-buffered W tiles
   C(*Cs)[RT + 1] = reinterpret_cast<C(*)[RT + 1]>(smem_raw);   // output staging, reuses Bs after the product
-  const int node = blocks[2 * blockIdx.y], r0 = blocks[2 * blockIdx.y + 1];
+  const int node = blocks[2 * (blockIdx.y / split)];
+  const int r0 = blocks[2 * (blockIdx.y / split) + 1] + (int)(blockIdx.y % split) * RBV;
   const int p = blockIdx.z;
   const int c0 = blockIdx.x * RT;
   const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
   const int K = FWD ? ns : ns + nb;
   const int M = FWD ? ns + nb : ns;
+  if (r0 >= M) return;   // a split past the node's last row (uniform over the CTA)
   const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
   (void)b;
@@ -108,11 +118,11 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
   // independent loads in flight per thread
   constexpr int FB = 8;
   const int boff = a.node_boff[node];
-  for (int base = tid; base < K * RT; base += FB * TS_THREADS) {
+  for (int base = tid; base < K * RT; base += FB * NTH) {
     C v[FB];
 #pragma unroll
     for (int q = 0; q < FB; ++q) {
-      const int idx = base + q * TS_THREADS;
+      const int idx = base + q * NTH;
       const int i = idx % K, cc = idx / K;
       const int c = c0 + cc;
       v[q] = mk<C>(0, 0);
@@ -127,13 +137,13 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
     }
 #pragma unroll
     for (int q = 0; q < FB; ++q) {
-      const int idx = base + q * TS_THREADS;
+      const int idx = base + q * NTH;
       if (idx < K * RT) Bs[(idx % K) * RT + idx / K] = v[q];
     }
   }
   __syncthreads();
-  // ---- product: rows r0 .. r0 + RB - 1 of W times Bs
-  const int tr = tid / 8, tcg = tid % 8;   // 16 row groups x 8 column groups
+  // ---- product: rows r0 .. r0 + RBV - 1 of W times Bs
+  const int tr = tid / CG, tcg = tid % CG;   // RBV / 4 row groups x CG column groups
   C acc[4][TC];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -141,12 +151,12 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
     for (int j = 0; j < TC; ++j) acc[i][j] = mk<C>(0, 0);
   // W tiles: each thread holds WPT elements of the next tile in registers while the
   // current tile is consumed from shared memory (one barrier per k step)
-  constexpr int WPT = RB * KT / TS_THREADS;
+  constexpr int WPT = RBV * KT / NTH;
   C wreg[WPT];
   auto load_w = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < WPT; ++q) {
-      const int idx = tid + q * TS_THREADS;
+      const int idx = tid + q * NTH;
       const int kk = idx % KT, rr = idx / KT;   // k fastest: coalesced rows of W
       const int r = r0 + rr, k = k0 + kk;
       wreg[q] = (r < M && k < K) ? W[(size_t)r * K + k] : mk<C>(0, 0);
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
   for (int k0 = 0; k0 < K; k0 += KT, buf ^= 1) {
 #pragma unroll
     for (int q = 0; q < WPT; ++q) {
-      const int idx = tid + q * TS_THREADS;
+      const int idx = tid + q * NTH;
       As[buf][idx % KT][idx / KT] = wreg[q];
     }
     __syncthreads();
@@ -181,23 +191,23 @@ __global__ void __launch_bounds__(TS_THREADS) trsv_gemm_kernel(TrsvArgs a, const
 #pragma unroll
     for (int j = 0; j < TC; ++j) Cs[tr * 4 + i][tcg * TC + j] = acc[i][j];
   __syncthreads();
-  const int rows = min(RB, M - r0);
+  const int rows = min(RBV, M - r0);
   if (FWD) {
     // y rows (ND order, rr fastest) and update rows (system fastest)
     const int ny = max(0, min(rows, ns - r0));
-    for (int idx = tid; idx < ny * RT; idx += TS_THREADS) {
+    for (int idx = tid; idx < ny * RT; idx += NTH) {
       const int rr = idx % ny, cc = idx / ny;
       const int c = c0 + cc;
       if (c < a.N) ynd[((size_t)p * a.N + c) * a.n + off + r0 + rr] = Cs[rr][cc];
     }
     const int uoff = a.node_uoff[node];
-    for (int idx = tid; idx < (rows - ny) * RT; idx += TS_THREADS) {
+    for (int idx = tid; idx < (rows - ny) * RT; idx += NTH) {
       const int cc = idx % RT, rr = ny + idx / RT;
       const int c = c0 + cc;
       if (c < a.N) u[(size_t)(uoff + r0 + rr - ns) * a.S + (size_t)p * a.N + c] = Cs[rr][cc];
     }
   } else {
-    for (int idx = tid; idx < rows * RT; idx += TS_THREADS) {
+    for (int idx = tid; idx < rows * RT; idx += NTH) {
       const int rr = idx % rows, cc = idx / rows;
       const int c = c0 + cc;
       if (c >= a.N) continue;
@@ -401,47 +411,75 @@ size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb) {
   return std::max((size_t)(max_ns + max_nb) * RT, (size_t)RB * (RT + 1)) * cs + stat;   // dynamic + static
 }
 
-template <typename T>
-static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P, const void* b, void* ynd,
-                         void* u, void* x, const void* factor, const int* active, size_t smem_total,
-                         cudaStream_t st) {
+template <typename T, bool FWD, int RBV, int RTV, int NTH>
+static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
+                                const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
+                                cudaStream_t st) {
   using C = cx_t<T>;
+  auto k = trsv_gemm_kernel<T, FWD, RBV, RTV, NTH>;
+  cudaError_t e = raise_smem_limit((const void*)k);
+  if (e != cudaSuccess) return e;
+  // CTAs per 64-row host block: enough RBV-row tiles to cover min(64, mmax) rows
+  const int split = (std::min(RB, mmax) + RBV - 1) / RBV;
+  const dim3 grid((a.N + RTV - 1) / RTV, count * split, P);
+  const size_t sm = std::max((size_t)kmax * RTV, (size_t)RBV * (RTV + 1)) * sizeof(C);
+  k<<<grid, NTH, sm, st>>>(a, blocks, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)factor, active, split);
+  return cudaGetLastError();
+}
+
+// Tile choice per level from its largest row count mmax (M = ns + nb forward, ns backward)
+// and its CTA count: 16-row tiles for the thin bottom separators (7 and 15 rows in 2D),
+// 32 x RT/2 tiles where 64 x RT leaves the GPU underfilled, else 64 x RT.
+template <typename T, bool FWD>
+static cudaError_t run_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
+                             const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
+                             cudaStream_t st) {
   constexpr int RT = TrsvCfg<T>::RT;
+  if (mmax <= 16)
+    return launch_level<T, FWD, 16, RT, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, factor, active, st);
+  const long ctas = (long)count * ((a.N + RT - 1) / RT) * P;
+  if (ctas >= 8 * 152 && mmax > 32)
+    return launch_level<T, FWD, 64, RT, 128>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, factor, active, st);
+  return launch_level<T, FWD, 32, RT / 2, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, factor, active, st);
+}
+
+template <typename T>
+static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
+                         const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
+                         size_t smem_total, cudaStream_t st) {
+  using C = cx_t<T>;
   (void)smem_total;
-  for (const void* f : {(const void*)trsv_gemm_kernel<T, true>, (const void*)trsv_gemm_kernel<T, false>,
-                        (const void*)leaf_kernel<T, true>, (const void*)leaf_kernel<T, false>}) {
+  auto leaf_f = leaf_kernel<T, true>;
+  auto leaf_b = leaf_kernel<T, false>;
+  for (const void* f : {(const void*)leaf_f, (const void*)leaf_b}) {
     cudaError_t e = raise_smem_limit(f);
     if (e != cudaSuccess) return e;
   }
-  const int tiles = (a.N + RT - 1) / RT;
   const bool leaves = la.nleaves > 0;
   const size_t lsm = leaf_smem_bytes<T>(la.max_ns, la.max_nb, la.bw);
   const dim3 lgrid((a.N + LT - 1) / LT, la.nleaves, P);
   if (leaves && (phases & SPP_LEAF_FWD)) {
-    leaf_kernel<T, true><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
+    leaf_f<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
   }
-  // dynamic shared memory sized per level (the root fronts need ~100 KB)
   for (int h = leaves ? 1 : 0; h < lv.nlevels && (phases & SPP_LEVELS_FWD); ++h) {
     if (lv.fcount[h] == 0) continue;
     if (lv.ucount[h] > 0) {
-      const dim3 agrid((lv.ucount[h] + 31) / 32, (unsigned)((a.S + 31) / 32));
-      assemble_kernel<T><<<agrid, 256, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], (const C*)b, (const C*)u,
-                                                (C*)x, active);
+      const dim3 agrid((lv.ucount[h] + AS_I - 1) / AS_I, (unsigned)((a.S + 31) / 32));
+      assemble_kernel<T><<<agrid, AS_I * 32, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], (const C*)b,
+                                                       (const C*)u, (C*)x, active);
     }
-    dim3 grid(tiles, lv.fcount[h], P);
-    const size_t sm = (size_t)std::max(lv.fkmax[h] * RT, RB * (RT + 1)) * sizeof(C);
-    trsv_gemm_kernel<T, true><<<grid, TS_THREADS, sm, st>>>(a, lv.fblocks + 2 * lv.fstart[h], (const C*)b, (C*)ynd,
-                                                            (C*)u, (C*)x, (const C*)factor, active);
+    cudaError_t e = run_level<T, true>(a, lv.fblocks + 2 * lv.fstart[h], lv.fcount[h], lv.fkmax[h], lv.bkmax[h], P,
+                                       b, ynd, u, x, factor, active, st);
+    if (e != cudaSuccess) return e;
   }
   for (int h = lv.nlevels - 1; h >= (leaves ? 1 : 0) && (phases & SPP_LEVELS_BWD); --h) {
     if (lv.bcount[h] == 0) continue;
-    dim3 grid(tiles, lv.bcount[h], P);
-    const size_t sm = (size_t)std::max(lv.bkmax[h] * RT, RB * (RT + 1)) * sizeof(C);
-    trsv_gemm_kernel<T, false><<<grid, TS_THREADS, sm, st>>>(a, lv.bblocks + 2 * lv.bstart[h], (const C*)b, (C*)ynd,
-                                                             (C*)u, (C*)x, (const C*)factor, active);
+    cudaError_t e = run_level<T, false>(a, lv.bblocks + 2 * lv.bstart[h], lv.bcount[h], lv.bkmax[h], lv.fkmax[h], P,
+                                        b, ynd, u, x, factor, active, st);
+    if (e != cudaSuccess) return e;
   }
   if (leaves && (phases & SPP_LEAF_BWD))
-    leaf_kernel<T, false><<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
+    leaf_b<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
   return cudaGetLastError();
 }
 

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
 // once per CTA.  Global accesses are cooperative, leaf index fastest (a warp touches
 // whole x-runs of one system's column), each one load behind an index already in shared
 // memory; only the substitutions run one thread per right-hand side, on shared memory.
-constexpr int LT = 64;        // right-hand sides per CTA for the leaves
+constexpr int LT = 128;       // right-hand sides per CTA for the leaves
 constexpr int LDY = LT + 1;   // padded stride: the leaf-index-fastest accesses hit distinct banks
 constexpr int LNB = 9;        // couplings per row of F_BS / F_SB (3^2 stencil)
 constexpr int LGB = 8;        // gathered loads in flight per thread

@@ -191,9 +191,30 @@ omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double*
 omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncols);
 
 /* Pole-expansion preconditioner on N columns: Y = sum_j w_j Y_j with Y_j the GMRES
- * solution of (H - sigma - z_j) Y_j = R started from R (Sec. 3.1 eqs. direct, lst).
+ * solution of (H - sigma - z_j) Y_j = R started from R (Sec. 3.1 eqs. direct, lst); with a
+ * projector built (omm_build_projector), Y = U U^* R.
  * R, Y device blocks of N columns.  st may be NULL (fills the gmres_* fields). */
 omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
+
+/* Precomputed preconditioner (Sec. 3.3, Algorithm 2): Y = sum_j w_j Y_j with
+ * (H - sigma - z_j) Y_j = B solved by the handle's GMRES (started from B), U = an orthonormal
+ * basis of N dominant columns of Y (rank-revealing step: Cholesky of Y^* Y with diagonal
+ * pivoting, the Gram form of QR with column pivoting; then Cholesky QR; all in FP64, U
+ * stored in the handle precision), and from then on the handle's preconditioner is U U^*
+ * (omm_iterate, omm_filter, omm_solve, omm_pole_solve): one Gram U^* R and one block update
+ * U (U^* R) per application instead of the pole solves.
+ * B: device, n x ncols, handle precision, a Gaussian block (real for real orbitals);
+ * ncols = N (k = 0 extra columns, as in the paper's experiments) or 2N (k = N: the pivoting
+ * then picks well-conditioned columns, which keeps the GMRES error of Y from being
+ * amplified by the conditioning of a square random block).  Costs ncols / N pole solves.
+ * st may be NULL (fills the gmres_* fields of the pole solves).
+ * Errors: OMM_ESTATE without poles; OMM_EINVAL for another ncols or if Y is numerically
+ * rank deficient (a Cholesky pivot <= 0). */
+omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st);
+
+/* Return to the pole-expansion preconditioner (frees nothing; U is kept until the next
+ * omm_build_projector or omm_destroy). */
+omm_status omm_drop_projector(omm_t h);
 
 /* Statistics of the sparsifying factor of pole j (host outputs, any may be NULL):
  * number of supernodes, factor entries (L + U), smallest |pivot| / largest |pivot|,

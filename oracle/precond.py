@@ -5,6 +5,8 @@ Sec. 3.1 eqs. direct and lst: G_m = -sum_j w_j Y_{m,j}, (H - z_j) Y_{m,j} = G(X_
 Y_{m,j} a rough GMRES solution started from the right-hand side.  Sec. 4: the same
 operator filters the starting guess once (X_1 = P X_0) before the CG.
 
+ProjectorPreconditioner: the precomputed U U^* of Sec. 3.3 (Algorithm 2).
+
 Modes
   'exact'  dense LU solve of every shifted system (n small): the projector r(H) itself
   'gmres'  GMRES per pole, inner right preconditioner 'spp' (sparsifying, Sec. 3.2),
@@ -63,3 +65,25 @@ class PolePreconditioner:
         for j in range(len(self.z)):
             out += self.w[j] * self.solve_pole(j, R)
         return out
+
+
+class ProjectorPreconditioner:
+    """The precomputed preconditioner U U^* of Sec. 3.3 (Algorithm 2), B with N + k columns
+    (the paper's experiments use k = 0, B of size n x N):
+      1. Y = sum_j w_j Y_j with (H - z_j) Y_j = B (pole: a PolePreconditioner, any mode);
+      2. rank-revealing QR of Y (column pivoting), U = its first N orthonormal columns;
+      3. the preconditioner is R -> U U^* R.
+    Blocks are row-stored (N, n) like everywhere in the oracle: row j is column j."""
+
+    def __init__(self, pole, B, N=None):
+        """B: (N + k, n) Gaussian block; N: the number of columns kept (default: all of B,
+        k = 0)."""
+        import scipy.linalg as sla
+        Y = pole(np.atleast_2d(B))
+        N = Y.shape[0] if N is None else N
+        Q, _, _ = sla.qr(Y.T, mode="economic", pivoting=True)
+        self.U = np.ascontiguousarray(Q[:, :N].T)          # row-stored, orthonormal rows
+
+    def __call__(self, R):
+        R = np.atleast_2d(R)
+        return (R @ self.U.conj().T) @ self.U               # columns: U (U^* R)

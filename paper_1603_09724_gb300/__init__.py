@@ -59,6 +59,8 @@ _SIGS = {
     "omm_poles_circle": (C.c_int, [C.c_double, C.c_double, C.c_int, _dp, _dp]),
     "omm_set_poles": (C.c_int, [_vp, C.c_int, _dp, _dp]),
     "omm_set_orbitals": (C.c_int, [_vp, _vp]),
+    "omm_build_projector": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(omm_stats)]),
+    "omm_drop_projector": (C.c_int, [_vp]),
     "omm_get_orbitals": (C.c_int, [_vp, _vp]),
     "omm_filter": (C.c_int, [_vp]),
     "omm_iterate": (C.c_int, [_vp, C.c_int, C.POINTER(omm_stats)]),
@@ -274,6 +276,19 @@ class Solver:
         check(lib.omm_pole_solve(self.h, self._t(R, self.N), self._t(Y), C.byref(st)), "omm_pole_solve")
         self.torch.cuda.current_stream().synchronize()
         return Y, st.as_dict()
+
+    def build_projector(self, B):
+        """Algorithm 2: U = orthonormal basis of N dominant columns of the pole expansion
+        applied to B (N or 2N columns, row-stored (cols, n)); the handle then preconditions
+        with U U^*."""
+        st = omm_stats()
+        cols = B.shape[0]
+        check(lib.omm_build_projector(self.h, self._t(B, cols), cols, C.byref(st)), "omm_build_projector")
+        self.torch.cuda.current_stream().synchronize()
+        return st.as_dict()
+
+    def drop_projector(self):
+        check(lib.omm_drop_projector(self.h), "omm_drop_projector")
 
     def factor_info(self, pole):
         ns, nnz, pr, npt = C.c_int(), C.c_longlong(), C.c_double(), C.c_int()

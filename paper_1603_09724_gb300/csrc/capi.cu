@@ -114,6 +114,16 @@ struct omm_ctx {
   int P = 0;
   std::vector<double2> z, w;   // the poles solved (conjugate pairs folded for real orbitals)
   bool real_combine = false;   // pole sum keeps 2 Re(w Y) of each folded pair
+  // precomputed preconditioner U U^* (Algorithm 2)
+  bool use_proj = false;
+  void* Uproj = nullptr;        // n x N, orthonormal columns
+  void* projM = nullptr;        // N x N working-precision coefficient block
+  void* projZero = nullptr;     // N x N zeros (second operand of the block update)
+  double2* projC = nullptr;     // up to 2N x 2N FP64 Gram
+  void* projY64 = nullptr;      // 3 x n x N complex128: [Y1 | Y2] being orthonormalised and a product
+  void* projM64 = nullptr;      // 2N x N complex128 coefficient block
+  void* projZero64 = nullptr;   // N x N complex128 zeros
+  void* projWork64 = nullptr;   // FP64 Gram work
   bool poles_set = false;
   // GMRES work (sized for P poles)
   int Palloc = 0;
@@ -616,6 +626,25 @@ omm_status gram_any(omm_ctx* h, const void* A, int na, const void* B, int nb, do
   return cuda_status(launch_gram(h->dbl, A, na, B, nb, h->n, C, ldc, cc_work, h->st), "gram");
 }
 
+// out = sign * U (U^* R): the precomputed preconditioner (one Gram, one block update)
+omm_status apply_projector(omm_ctx* h, const void* R, void* out, double sign) {
+  const int N = h->N;
+  const double cnt = (double)N * h->n;
+  PROF(PC_GRAM, 2.0 * cnt * h->csz, 2, gram_any(h, h->Uproj, N, R, N, h->projC, N, h->gram_work));
+  PROF(PC_SMALL, 0, 1, cuda_status(launch_gram_to_matrix(h->dbl, h->projC, N, N, sign, h->projM, h->st), "projM"));
+  PROF(PC_BLOCKUPD, 2.0 * cnt * h->csz, 1,
+       cuda_status(launch_block_update(h->dbl, h->Uproj, h->Uproj, h->projM, h->projZero, 0.0, 0.0, N, h->n, out,
+                                       h->st),
+                   "proj"));
+  return OMM_OK;
+}
+
+// The preconditioner of the handle: U U^* once built, else the pole expansion
+omm_status precondition(omm_ctx* h, const void* R, void* out, double sign) {
+  if (h->use_proj) return apply_projector(h, R, out, sign);
+  return pole_solve(h, R, out, sign);
+}
+
 // Grams of the current X and the gradient update matrices (t = 0)
 omm_status start_cg(omm_ctx* h) {
   OMM_TRY(happly(h, h->X(), h->HX(), h->N, h->zero_shift, h->N, nullptr));
@@ -636,7 +665,7 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
     PROF(PC_BLOCKUPD, 3.0 * cnt * h->csz, 1,
          cuda_status(launch_block_update(h->dbl, h->X(), h->HX(), h->M1, h->M2, 0.0, 2.0, h->N, h->n, h->Grad, h->st),
                      "grad"));
-    OMM_TRY(pole_solve(h, h->Grad, h->G, -1.0));
+    OMM_TRY(precondition(h, h->Grad, h->G, -1.0));
     PROF(PC_VEC, 2.0 * cnt * h->csz, 2,
          cuda_status(launch_redot(h->dbl, cnt, h->G, h->G, &h->sc->gg, h->red_work, h->st), "dot"));
     if (it > 0)
@@ -661,8 +690,10 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
          cuda_status(launch_axpby(h->dbl, cnt, &h->sc->t_c, h->HD(), &h->sc->one_c, h->HX(), h->st), "upd"));
     std::swap(h->G, h->Gp);
     OMM_TRY(read_scalars(h));
-    OMM_TRY(gmres_stats(h));
-    h->gmres_total += h->last_gmres_max;
+    if (!h->use_proj) {
+      OMM_TRY(gmres_stats(h));
+      h->gmres_total += h->last_gmres_max;
+    }
     if (h->sc_h->bad) {
       *done_iters = it + 1;
       return OMM_ESHIFT;
@@ -1050,6 +1081,7 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
     w = wf.data();
   }
   h->real_combine = h->prm.real_orbitals != 0;
+  h->use_proj = false;   // a projector built from other poles no longer applies
   h->P = P;
   h->z.resize(P);
   h->w.resize(P);
@@ -1138,7 +1170,7 @@ omm_status omm_get_orbitals(omm_t h, void* X) {
 omm_status omm_filter(omm_t h) {
   if (!h) return OMM_EINVAL;
   if (!h->poles_set) return OMM_ESTATE;
-  OMM_TRY(pole_solve(h, h->X(), h->G, +1.0));
+  OMM_TRY(precondition(h, h->X(), h->G, +1.0));
   return cuda_status(cudaMemcpyAsync(h->X(), h->G, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "copy");
 }
 
@@ -1261,13 +1293,197 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
 omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st) {
   if (!h || !R || !Y) return OMM_EINVAL;
   if (!h->poles_set) return OMM_ESTATE;
-  OMM_TRY(pole_solve(h, R, Y, 1.0));
-  OMM_TRY(gmres_stats(h));
+  OMM_TRY(precondition(h, R, Y, 1.0));
+  if (!h->use_proj) OMM_TRY(gmres_stats(h));
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->gmres_iters_max = h->last_gmres_max;
     st->gmres_relres_max = h->last_relres_max;
   }
+  return OMM_OK;
+}
+
+// Host Cholesky of the Hermitian positive definite N x N matrix S (row-major FP64) and the
+// inverse of its upper factor: S = R^* R, Ri = R^-1.  False if a pivot is not positive.
+static bool chol_inverse(const double2* S, int ldS, int N, std::vector<cd>& Ri) {
+  std::vector<cd> R((size_t)N * N, cd(0.0, 0.0));
+  for (int j = 0; j < N; ++j) {
+    double d = S[(size_t)j * ldS + j].x;
+    for (int k = 0; k < j; ++k) d -= std::norm(R[(size_t)k * N + j]);
+    if (!(d > 0.0)) return false;
+    const double rjj = std::sqrt(d);
+    R[(size_t)j * N + j] = rjj;
+    for (int i = j + 1; i < N; ++i) {
+      cd acc(S[(size_t)j * ldS + i].x, S[(size_t)j * ldS + i].y);
+      for (int k = 0; k < j; ++k) acc -= std::conj(R[(size_t)k * N + j]) * R[(size_t)k * N + i];
+      R[(size_t)j * N + i] = acc / rjj;
+    }
+  }
+  Ri.assign((size_t)N * N, cd(0.0, 0.0));
+  for (int c = 0; c < N; ++c) {
+    Ri[(size_t)c * N + c] = 1.0 / R[(size_t)c * N + c];
+    for (int r = c - 1; r >= 0; --r) {
+      cd acc(0.0, 0.0);
+      for (int k = r + 1; k <= c; ++k) acc += R[(size_t)r * N + k] * Ri[(size_t)k * N + c];
+      Ri[(size_t)r * N + c] = -acc / R[(size_t)r * N + r];
+    }
+  }
+  return true;
+}
+
+// Rank-revealing step on the Gram G = Y^* Y of K columns (row-major FP64): Cholesky with
+// diagonal pivoting for N steps (the Gram form of QR with column pivoting).  Returns the
+// chosen columns piv[0..N) and the K x N coefficient block M (row-major) with
+// Y M = Y(:, piv) R11^-1, an orthonormal basis of the chosen columns.
+static bool pivoted_select(const std::vector<double2>& Gd, int K, int N, std::vector<int>& piv,
+                           std::vector<cd>& M) {
+  std::vector<cd> G((size_t)K * K);
+  for (size_t e = 0; e < G.size(); ++e) G[e] = cd(Gd[e].x, Gd[e].y);
+  piv.resize(K);
+  for (int i = 0; i < K; ++i) piv[i] = i;
+  std::vector<cd> R((size_t)N * K, cd(0.0, 0.0));   // rows of the pivoted factor (in original column order)
+  std::vector<double> dg(K);
+  for (int i = 0; i < K; ++i) dg[i] = G[(size_t)i * K + i].real();
+  for (int j = 0; j < N; ++j) {
+    int best = j;
+    for (int i = j + 1; i < K; ++i)
+      if (dg[piv[i]] > dg[piv[best]]) best = i;
+    std::swap(piv[j], piv[best]);
+    const int pj = piv[j];
+    if (!(dg[pj] > 0.0)) return false;
+    const double rjj = std::sqrt(dg[pj]);
+    R[(size_t)j * K + pj] = rjj;
+    for (int i = j + 1; i < K; ++i) {
+      const int pi = piv[i];
+      cd acc = G[(size_t)pj * K + pi];
+      for (int k = 0; k < j; ++k) acc -= std::conj(R[(size_t)k * K + pj]) * R[(size_t)k * K + pi];
+      R[(size_t)j * K + pi] = acc / rjj;
+      dg[pi] -= std::norm(R[(size_t)j * K + pi]);
+    }
+  }
+  // R11 (N x N upper, in pivot order) and its inverse
+  std::vector<cd> R11((size_t)N * N, cd(0.0, 0.0)), Ri((size_t)N * N, cd(0.0, 0.0));
+  for (int r = 0; r < N; ++r)
+    for (int c = r; c < N; ++c) R11[(size_t)r * N + c] = R[(size_t)r * K + piv[c]];
+  for (int c = 0; c < N; ++c) {
+    Ri[(size_t)c * N + c] = 1.0 / R11[(size_t)c * N + c];
+    for (int r = c - 1; r >= 0; --r) {
+      cd acc(0.0, 0.0);
+      for (int k = r + 1; k <= c; ++k) acc += R11[(size_t)r * N + k] * Ri[(size_t)k * N + c];
+      Ri[(size_t)r * N + c] = -acc / R11[(size_t)r * N + r];
+    }
+  }
+  M.assign((size_t)K * N, cd(0.0, 0.0));
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < N; ++c) M[(size_t)piv[r] * N + c] = Ri[(size_t)r * N + c];
+  piv.resize(N);
+  return true;
+}
+
+omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st) {
+  if (!h || !B) return OMM_EINVAL;
+  if (!h->poles_set) return OMM_ESTATE;
+  const int N = h->N;
+  if (ncols != N && ncols != 2 * N) return OMM_EINVAL;
+  const size_t cnt = (size_t)N * h->n;
+  if (!h->Uproj) {
+    OMM_TRY(h->dalloc(&h->Uproj, cnt * h->csz));
+    OMM_TRY(h->dalloc(&h->projM, (size_t)N * N * h->csz));
+    OMM_TRY(h->dalloc(&h->projZero, (size_t)N * N * h->csz));
+    OMM_TRY(h->dalloc_t(&h->projC, (size_t)4 * N * N * sizeof(double2)));
+    OMM_TRY(cuda_status(cudaMemsetAsync(h->projZero, 0, (size_t)N * N * h->csz, h->st), "memset"));
+    // FP64: [Y1 | Y2 | T] blocks, the coefficient blocks and the Gram work
+    OMM_TRY(h->dalloc(&h->projY64, 3 * cnt * 16));
+    OMM_TRY(h->dalloc(&h->projM64, (size_t)2 * N * N * 16));
+    OMM_TRY(h->dalloc(&h->projZero64, (size_t)N * N * 16));
+    OMM_TRY(h->dalloc(&h->projWork64, gram_work_bytes(2 * N, 2 * N, h->n)));
+    OMM_TRY(cuda_status(cudaMemsetAsync(h->projZero64, 0, (size_t)N * N * 16, h->st), "memset"));
+  }
+  h->use_proj = false;
+  void* Y64 = h->projY64;                      // Y1, then Y2 at + cnt (2N contiguous columns)
+  void* T64 = (char*)h->projY64 + 2 * cnt * 16;
+  // Y = sum_j w_j (H - sigma - z_j)^-1 B  (Algorithm 2: the pole solves), N columns at a time
+  int gmax = 0;
+  double rmax = 0.0;
+  for (int part = 0; part < ncols / N; ++part) {
+    OMM_TRY(pole_solve(h, (const char*)B + part * cnt * h->csz, h->Uproj, 1.0));
+    OMM_TRY(gmres_stats(h));
+    gmax = std::max(gmax, h->last_gmres_max);
+    rmax = std::max(rmax, h->last_relres_max);
+    void* dst = (char*)Y64 + part * cnt * 16;
+    if (h->dbl)
+      OMM_TRY(cuda_status(cudaMemcpyAsync(dst, h->Uproj, cnt * 16, cudaMemcpyDeviceToDevice, h->st), "copy"));
+    else
+      PROF(PC_VEC, 24.0 * cnt, 1, cuda_status(launch_convert(true, cnt, h->Uproj, dst, h->st), "convert"));
+  }
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->gmres_iters_max = gmax;
+    st->gmres_relres_max = rmax;
+  }
+  // Everything below is FP64 (the block, the Grams, the factors and the products): the
+  // orthonormal basis U = Y(:, chosen) R^-1 amplifies the rounding of Y by cond(R).
+  const int K = ncols;
+  std::vector<double2> S((size_t)K * K);
+  auto gram64 = [&](int cols) -> omm_status {
+    PROF(PC_GRAM, 2.0 * cols * h->n * 16, 2,
+         cuda_status(launch_gram(true, Y64, cols, Y64, cols, h->n, h->projC, cols, h->projWork64, h->st), "gram64"));
+    OMM_TRY(cuda_status(cudaMemcpyAsync(S.data(), h->projC, (size_t)cols * cols * sizeof(double2),
+                                        cudaMemcpyDeviceToHost, h->st),
+                        "gram d2h"));
+    return cuda_status(cudaStreamSynchronize(h->st), "sync");
+  };
+  auto apply64 = [&](const std::vector<cd>& Mtop, const std::vector<cd>* Mbot) -> omm_status {
+    // T = Y1 Mtop (+ Y2 Mbot), then Y1 = T
+    OMM_TRY(cuda_status(cudaMemcpyAsync(h->projM64, Mtop.data(), (size_t)N * N * 16, cudaMemcpyHostToDevice, h->st),
+                        "M h2d"));
+    void* M2 = h->projZero64;
+    const void* Yb = Y64;
+    if (Mbot) {
+      M2 = (char*)h->projM64 + (size_t)N * N * 16;
+      OMM_TRY(cuda_status(cudaMemcpyAsync(M2, Mbot->data(), (size_t)N * N * 16, cudaMemcpyHostToDevice, h->st),
+                          "M h2d"));
+      Yb = (const char*)Y64 + cnt * 16;
+    }
+    PROF(PC_BLOCKUPD, (Mbot ? 3.0 : 2.0) * cnt * 16, 1,
+         cuda_status(launch_block_update(true, Y64, Yb, h->projM64, M2, 0.0, 0.0, N, h->n, T64, h->st), "qr"));
+    OMM_TRY(cuda_status(cudaMemcpyAsync(Y64, T64, cnt * 16, cudaMemcpyDeviceToDevice, h->st), "copy"));
+    return cuda_status(cudaStreamSynchronize(h->st), "sync");   // the host vectors are reused
+  };
+  int passes = 2;   // Cholesky QR passes on N columns
+  if (K == 2 * N) {
+    // rank-revealing step: the N dominant columns of [Y1 Y2] and their orthonormal basis
+    OMM_TRY(gram64(K));
+    std::vector<int> piv;
+    std::vector<cd> M;
+    if (!pivoted_select(S, K, N, piv, M)) {
+      omm_internal_set_message("omm_build_projector: the filtered block is rank deficient");
+      return OMM_EINVAL;
+    }
+    std::vector<cd> Mt(M.begin(), M.begin() + (size_t)N * N), Mb(M.begin() + (size_t)N * N, M.end());
+    OMM_TRY(apply64(Mt, &Mb));
+    passes = 1;   // one more pass restores orthogonality to FP64 rounding
+  }
+  std::vector<cd> Ri;
+  for (int pass = 0; pass < passes; ++pass) {
+    OMM_TRY(gram64(N));
+    if (!chol_inverse(S.data(), N, N, Ri)) {
+      omm_internal_set_message("omm_build_projector: the filtered block is rank deficient");
+      return OMM_EINVAL;
+    }
+    OMM_TRY(apply64(Ri, nullptr));
+  }
+  if (h->dbl)
+    OMM_TRY(cuda_status(cudaMemcpyAsync(h->Uproj, Y64, cnt * 16, cudaMemcpyDeviceToDevice, h->st), "copy"));
+  else
+    PROF(PC_VEC, 24.0 * cnt, 1, cuda_status(launch_convert(false, cnt, Y64, h->Uproj, h->st), "convert"));
+  h->use_proj = true;
+  return OMM_OK;
+}
+
+omm_status omm_drop_projector(omm_t h) {
+  if (!h) return OMM_EINVAL;
+  h->use_proj = false;
   return OMM_OK;
 }
 

@@ -219,3 +219,26 @@ cudaError_t launch_pr_beta(OmmScalars* sc, int first, cudaStream_t st) {
 }
 
 }  // namespace omm
+
+namespace omm {
+
+// M = scale * C for an N x N FP64 Gram C (row stride ldc), in the working precision
+template <typename T>
+__global__ void gram_to_matrix_kernel(const double2* __restrict__ C, int ldc, int N, double scale,
+                                      cx_t<T>* __restrict__ M) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N; idx += gridDim.x * blockDim.x) {
+    const double2 c = C[(size_t)(idx / N) * ldc + idx % N];
+    M[idx] = mk<cx_t<T>>((T)(scale * c.x), (T)(scale * c.y));
+  }
+}
+
+cudaError_t launch_gram_to_matrix(bool dbl, const double2* C, int ldc, int N, double scale, void* M, cudaStream_t st) {
+  const int blocks = (N * N + 255) / 256 < 1024 ? (N * N + 255) / 256 : 1024;
+  if (dbl)
+    gram_to_matrix_kernel<double><<<blocks, 256, 0, st>>>(C, ldc, N, scale, (double2*)M);
+  else
+    gram_to_matrix_kernel<float><<<blocks, 256, 0, st>>>(C, ldc, N, scale, (float2*)M);
+  return cudaGetLastError();
+}
+
+}  // namespace omm

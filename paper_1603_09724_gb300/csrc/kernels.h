@@ -76,6 +76,8 @@ struct OmmScalars {
 cudaError_t launch_line_search(bool dbl, const double2* C, int N, double sigma, int have_d, double tol,
                                OmmScalars* sc, void* M1, void* M2, cudaStream_t st);
 // beta = (gg - gdot) / ggp (Polak-Ribiere); first == 1 sets beta = 0.
+// M = scale * C (N x N FP64 Gram with row stride ldc) in the working precision
+cudaError_t launch_gram_to_matrix(bool dbl, const double2* C, int ldc, int N, double scale, void* M, cudaStream_t st);
 cudaError_t launch_pr_beta(OmmScalars* sc, int first, cudaStream_t st);
 
 // ---- k_krylov.cu: batched restarted GMRES over S systems of length n

@@ -43,3 +43,32 @@ def test_host_only_entry_points_work_without_gpu():
     with pytest.raises(omm.OmmError):
         omm.poles_fermi(-1.0, 1.0, 2.0, 7)   # odd P
     assert np.all(np.isfinite(w))
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    """omm_create validates its arguments on the host before any allocation: a shift that
+    leaves H - sigma indefinite (Sec. 1: E_omm is then unbounded below), an unsupported grid
+    size, malformed parameters."""
+    import ctypes as C
+    import numpy as np
+    import paper_1603_09724_gb300 as omm
+    m, L = 16, 10.0
+    V = np.zeros(m * m)
+    Vp = V.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+
+    def create(grid, shift, prm=None, Np=4):
+        return omm.lib.omm_create(C.byref(grid), Vp, Np, shift, C.byref(prm) if prm is not None else None, None,
+                                  C.byref(h))
+
+    g = omm.make_grid(2, m, L)
+    tmax = 2 * np.pi ** 2 / L ** 2 * 2 * (m // 2) ** 2
+    assert create(g, 0.5 * tmax) == omm.OMM_ESHIFT
+    assert create(omm.make_grid(2, 14, L), 2 * tmax) == omm.OMM_EUNSUPPORTED    # 14 = 2 * 7
+    assert create(omm.make_grid(4, m, L), 2 * tmax) == omm.OMM_EINVAL
+    bad = omm.default_params(gmres_m=0)
+    assert create(g, 2 * tmax, bad) == omm.OMM_EINVAL
+    bad = omm.default_params(stencil_radius=2)
+    assert create(g, 2 * tmax, bad) == omm.OMM_EINVAL
+    assert create(g, 2 * tmax, None, Np=0) == omm.OMM_EINVAL
+    assert not h.value

@@ -30,7 +30,8 @@ constexpr int KT = 16;   // k step of the product
 
 // Forward right-hand sides of one tree height: r_S = b_S - (sum of the update rows of the
 // descendants that target S, in CSR order), for every unknown of the height and every
-// active system, written in ND order into x (x is not read before the backward sweep,
+// active system of the launch (nsys = its poles x N; u rows have stride a.S, the systems of
+// all poles), written in ND order into x (x is not read before the backward sweep,
 // which overwrites every entry of an active system).  An AS_I x 32 tile (unknowns x
 // systems, one element per thread) is transposed through shared memory so that the gather
 // of b and the store into x run unknown-fastest while the update rows are read
@@ -40,7 +41,7 @@ constexpr int AS_I = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
-                                                              const cx_t<T>* __restrict__ b,
+                                                              size_t nsys, const cx_t<T>* __restrict__ b,
                                                               const cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
                                                               const int* __restrict__ active) {
   using C = cx_t<T>;
@@ -52,14 +53,14 @@ __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const i
     const int ii = t % AS_I, ss = t / AS_I;   // unknown fastest
     const int i = i0 + ii;
     const size_t s = s0 + ss;
-    if (i < cnt && s < a.S && (!active || active[s])) tile[ii][ss] = b[s * a.n + a.perm[lunk[i]]];
+    if (i < cnt && s < nsys && (!active || active[s])) tile[ii][ss] = b[s * a.n + a.perm[lunk[i]]];
   }
   __syncthreads();
   {
     const int ss = t % 32, ii = t / 32;       // system fastest
     const int i = i0 + ii;
     const size_t s = s0 + ss;
-    if (i < cnt && s < a.S && (!active || active[s])) {
+    if (i < cnt && s < nsys && (!active || active[s])) {
       const int nd = lunk[i];
       const int e0 = a.contrib_ptr[nd], e1 = a.contrib_ptr[nd + 1];
       C acc = tile[ii][ss];
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const i
     const int ii = t % AS_I, ss = t / AS_I;
     const int i = i0 + ii;
     const size_t s = s0 + ss;
-    if (i < cnt && s < a.S && (!active || active[s])) x[s * a.n + lunk[i]] = tile[ii][ss];
+    if (i < cnt && s < nsys && (!active || active[s])) x[s * a.n + lunk[i]] = tile[ii][ss];
   }
 }
 
@@ -464,8 +465,9 @@ static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, co
   for (int h = leaves ? 1 : 0; h < lv.nlevels && (phases & SPP_LEVELS_FWD); ++h) {
     if (lv.fcount[h] == 0) continue;
     if (lv.ucount[h] > 0) {
-      const dim3 agrid((lv.ucount[h] + AS_I - 1) / AS_I, (unsigned)((a.S + 31) / 32));
-      assemble_kernel<T><<<agrid, AS_I * 32, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], (const C*)b,
+      const size_t nsys = (size_t)P * a.N;   // systems of this launch (a.S is the row stride of u)
+      const dim3 agrid((lv.ucount[h] + AS_I - 1) / AS_I, (unsigned)((nsys + 31) / 32));
+      assemble_kernel<T><<<agrid, AS_I * 32, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], nsys, (const C*)b,
                                                        (const C*)u, (C*)x, active);
     }
     cudaError_t e = run_level<T, true>(a, lv.fblocks + 2 * lv.fstart[h], lv.fcount[h], lv.fkmax[h], lv.bkmax[h], P,

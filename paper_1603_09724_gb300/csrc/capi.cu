@@ -66,9 +66,10 @@ struct omm_ctx {
   bool dbl = true;
   size_t csz = 16;
   cudaStream_t st = nullptr;
-  // second stream for the triangular solves of half the poles (forked from and joined to st)
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // extra streams for the triangular solves of groups of poles (forked from and joined to st)
+  static constexpr int kTrsvStreams = 4;
+  cudaStream_t st2[kTrsvStreams] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kTrsvStreams] = {};
   void* (*alloc)(size_t, void*) = nullptr;
   void (*release)(void*, void*) = nullptr;
   void* alloc_ctx = nullptr;
@@ -219,8 +220,10 @@ struct omm_ctx {
     prof.pending.clear();
     for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
-    if (st2) cudaStreamDestroy(st2);
+    for (int i = 0; i < kTrsvStreams; ++i) {
+      if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+      if (st2[i]) cudaStreamDestroy(st2[i]);
+    }
     for (void* p : allocs) {
       if (release) release(p, alloc_ctx);
       else cudaFree(p);
@@ -504,37 +507,42 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   int nk = 0;
   for (int l = has_leaves ? 1 : 0; l < lv.nlevels; ++l)   // per height: (assembly +) product forward, product backward
     nk += (lv.fcount[l] > 0) * (1 + (lv.ucount[l] > 0)) + (lv.bcount[l] > 0);
-  // Two halves of the poles on two streams: the latency-bound top of the tree of one half
-  // overlaps the other half's work.  Every per-pole array is offset on the host; the update
+  // Groups of poles on their own streams: the latency-bound top of the tree of one group
+  // overlaps the other groups' work.  Every per-pole array is offset on the host; the update
   // rows keep their row stride S and are offset by columns.
-  const int Pa = (P >= 2) ? P / 2 : P;
-  if (Pa < P && !h->st2) {
-    OMM_TRY(cuda_status(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking), "stream"));
+  const int ng = std::min(P, (int)omm_ctx::kTrsvStreams);
+  if (ng > 1 && !h->st2[0]) {
     OMM_TRY(cuda_status(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event"));
-    OMM_TRY(cuda_status(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event"));
+    for (int g = 0; g < omm_ctx::kTrsvStreams; ++g) {
+      OMM_TRY(cuda_status(cudaStreamCreateWithFlags(&h->st2[g], cudaStreamNonBlocking), "stream"));
+      OMM_TRY(cuda_status(cudaEventCreateWithFlags(&h->ev_join[g], cudaEventDisableTiming), "event"));
+    }
   }
   auto spp = [&](int phases) -> omm_status {
-    if (Pa == P)
+    if (ng == 1)
       return cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, P, tmp, h->ynd, h->ubuf, Z, h->factor, active,
                                           h->trsv_smem, h->st),
                          "spp");
-    const size_t sys_b = (size_t)Pa * Ncols;   // first system of the second half
-    const size_t vec_b = sys_b * h->n * h->csz;
     OMM_TRY(cuda_status(cudaEventRecord(h->ev_fork, h->st), "fork"));
-    OMM_TRY(cuda_status(cudaStreamWaitEvent(h->st2, h->ev_fork, 0), "fork"));
-    OMM_TRY(cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, Pa, tmp, h->ynd, h->ubuf, Z, h->factor, active,
-                                         h->trsv_smem, h->st),
-                        "spp"));
-    OMM_TRY(cuda_status(
-        launch_spp_solve(phases, h->dbl, a, lv, leaf_args(h, Pa), P - Pa, (const char*)tmp + vec_b,
-                         (char*)h->ynd + vec_b, (char*)h->ubuf + sys_b * h->csz, (char*)Z + vec_b,
-                         (const char*)h->factor + (size_t)Pa * h->spp.factor_size * h->csz,
-                         active ? active + sys_b : nullptr, h->trsv_smem, h->st2),
-        "spp"));
-    OMM_TRY(cuda_status(cudaEventRecord(h->ev_join, h->st2), "join"));
-    return cuda_status(cudaStreamWaitEvent(h->st, h->ev_join, 0), "join");
+    int p0 = 0;
+    for (int g = 0; g < ng; ++g) {
+      const int pg = P / ng + (g < P % ng ? 1 : 0);   // poles of group g
+      const size_t sys0 = (size_t)p0 * Ncols;
+      const size_t vec0 = sys0 * h->n * h->csz;
+      OMM_TRY(cuda_status(cudaStreamWaitEvent(h->st2[g], h->ev_fork, 0), "fork"));
+      OMM_TRY(cuda_status(
+          launch_spp_solve(phases, h->dbl, a, lv, leaf_args(h, p0), pg, (const char*)tmp + vec0,
+                           (char*)h->ynd + vec0, (char*)h->ubuf + sys0 * h->csz, (char*)Z + vec0,
+                           (const char*)h->factor + (size_t)p0 * h->spp.factor_size * h->csz,
+                           active ? active + sys0 : nullptr, h->trsv_smem, h->st2[g]),
+          "spp"));
+      OMM_TRY(cuda_status(cudaEventRecord(h->ev_join[g], h->st2[g]), "join"));
+      OMM_TRY(cuda_status(cudaStreamWaitEvent(h->st, h->ev_join[g], 0), "join"));
+      p0 += pg;
+    }
+    return OMM_OK;
   };
-  const int ns = (Pa < P) ? 2 : 1;   // launches per kernel (one per stream)
+  const int ns = ng;   // launches per kernel (one per stream)
   if (has_leaves)
     PROF(PC_TRSV_LEAF, (h->tb_leaf_fwd_sys * Se + h->tb_leaf_pole * P) * cs, ns, spp(SPP_LEAF_FWD));
   PROF(PC_TRSV, (h->tb_lvl_sys * Se + h->tb_lvl_pole * P) * cs, ns * nk, spp(SPP_LEVELS_FWD | SPP_LEVELS_BWD));

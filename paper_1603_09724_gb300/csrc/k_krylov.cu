@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, cx_t<T>* 
                                                          const int* __restrict__ active) {
   using C = cx_t<T>;
   constexpr int k = KK - 1;
+  // loop unroll over the grid: more independent loads in flight when the basis is short
+  constexpr int UF = KK <= 2 ? 4 : (KK <= 6 ? 2 : 1);
   __shared__ double sh[(2 * KK + 1) * (KT / 32)];
   const int s = blockIdx.x;
   if (!active[s]) return;
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, cx_t<T>* 
   // sweep 1
 #pragma unroll
   for (int q = 0; q < KK; ++q) ht[q] = mk<C>(0, 0);
+#pragma unroll UF
   for (size_t i = threadIdx.x; i < n; i += KT) {
     const C wi = ws[i];
 #pragma unroll
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, cx_t<T>* 
 #pragma unroll
   for (int q = 0; q < KK; ++q) ht[q] = mk<C>(0, 0);
   T nw = 0;
+#pragma unroll UF
   for (size_t i = threadIdx.x; i < n; i += KT) {
     C wi = ws[i];
     C vv[KK];
@@ -189,6 +193,7 @@ __global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, cx_t<T>* 
   for (int j = 0; j < KK; ++j) h1c[j] = mk<C>((T)h1[2 * j], (T)h1[2 * j + 1]);
   // sweep 3
   C* vk1 = V + (size_t)(k + 1) * vs + (size_t)s * n;
+#pragma unroll UF
   for (size_t i = threadIdx.x; i < n; i += KT) {
     C wi = ws[i];
 #pragma unroll

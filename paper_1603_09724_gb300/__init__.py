@@ -34,7 +34,7 @@ class omm_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("inner", C.c_int), ("gmres_m", C.c_int), ("gmres_cycles", C.c_int),
                 ("gmres_rtol", C.c_double), ("gmres_fixed", C.c_int), ("stencil_radius", C.c_int),
                 ("pivot_floor", C.c_double), ("tol", C.c_double), ("maxit", C.c_int), ("refilter", C.c_int),
-                ("gram_tensor", C.c_int), ("real_orbitals", C.c_int)]
+                ("gram_tensor", C.c_int), ("real_orbitals", C.c_int), ("trsv_streams", C.c_int)]
 
 
 class omm_stats(C.Structure):

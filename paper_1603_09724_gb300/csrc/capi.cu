@@ -510,7 +510,7 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   // Groups of poles on their own streams: the latency-bound top of the tree of one group
   // overlaps the other groups' work.  Every per-pole array is offset on the host; the update
   // rows keep their row stride S and are offset by columns.
-  const int ng = std::min(P, (int)omm_ctx::kTrsvStreams);
+  const int ng = std::min(P, h->prm.trsv_streams > 0 ? h->prm.trsv_streams : (int)omm_ctx::kTrsvStreams);
   if (ng > 1 && !h->st2[0]) {
     OMM_TRY(cuda_status(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event"));
     for (int g = 0; g < omm_ctx::kTrsvStreams; ++g) {
@@ -952,6 +952,7 @@ omm_status omm_default_params(omm_params* p) {
   p->refilter = 0;
   p->gram_tensor = 0;
   p->real_orbitals = 0;
+  p->trsv_streams = 0;
   return OMM_OK;
 }
 
@@ -992,7 +993,7 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
   if (p) prm = *p;
   if (prm.gmres_m < 1 || prm.gmres_m > 15 || prm.gmres_cycles < 1 || prm.maxit < 0 || prm.refilter < 0 ||
       (prm.precision != OMM_FP64 && prm.precision != OMM_MIXED) || prm.inner < 0 || prm.inner > 2 ||
-      prm.stencil_radius != 1)
+      prm.stencil_radius != 1 || prm.trsv_streams < 0 || prm.trsv_streams > omm_ctx::kTrsvStreams)
     return OMM_EINVAL;
   const bool dbl = prm.precision == OMM_FP64;
   if (!fused_fft_supported(g->dim, m, dbl) && !big_fft_supported(g->dim, m)) return OMM_EUNSUPPORTED;

@@ -62,18 +62,49 @@ class _Resident:
         self.X = None      # device tensor of the last solution
 
 
+class TorchDevice:
+    """Device plumbing of the server (streams and host<->device copies) through PyTorch."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+
+    def set_device(self, i):
+        self.torch.cuda.set_device(i)
+
+    def new_stream(self):
+        return self.torch.cuda.Stream()
+
+    def stream_ctx(self, stream):
+        return self.torch.cuda.stream(stream)
+
+    def stream_handle(self, stream):
+        return stream.cuda_stream
+
+    def upload(self, arr, dtype):
+        return self.torch.from_numpy(np.ascontiguousarray(arr)).to(device="cuda", dtype=dtype, non_blocking=False)
+
+    def download(self, t):
+        return t.cpu().numpy()
+
+
 class OmmServer:
     """slots: concurrent solves; hbm_budget: bytes the resident handles may hold;
-    params: keyword overrides of omm_params (precision, tolerances ...)."""
+    params: keyword overrides of omm_params (precision, tolerances ...).
+    backend (default: this package) supplies Solver, default_params, poles_fermi and the
+    precision constants; device (default: TorchDevice) the streams and copies."""
 
-    def __init__(self, hbm_budget: int, slots: int = 4, device: int = 0, **params):
-        import torch
-        import paper_1603_09724_gb300 as omm
-        self.torch, self.omm = torch, omm
+    def __init__(self, hbm_budget: int, slots: int = 4, device: int = 0, backend=None, device_api=None,
+                 **params):
+        if backend is None:
+            import paper_1603_09724_gb300 as backend
+        self.omm = backend
+        self.dev = device_api if device_api is not None else TorchDevice()
         self.device = device
         self.budget = int(hbm_budget)
         self.slots = slots
-        self.params = dict(precision=omm.OMM_MIXED, maxit=40, tol=1e-10)
+        # one triangular-solve stream per handle: the server already overlaps handles
+        self.params = dict(precision=backend.OMM_MIXED, maxit=40, tol=1e-10, trsv_streams=1)
         self.params.update(params)
         self.resident: dict[str, _Resident] = {}
         self.shape_bytes: dict[tuple, int] = {}
@@ -91,6 +122,8 @@ class OmmServer:
 
     # ---------------------------------------------------------------- public
     def submit(self, req: Request) -> int:
+        if self._estimate(req) > self.budget:   # would wait forever for room
+            raise ValueError("request needs more device memory than the server's budget")
         with self.cv:
             req.rid = self.next_id
             self.next_id += 1
@@ -123,10 +156,13 @@ class OmmServer:
         return self.resident_bytes() + sum(self.reserved.values())
 
     # ---------------------------------------------------------------- internals
+    def _shape(self, req: Request):
+        return (req.dim, req.m, req.N, req.P, self.params.get("precision"))
+
     def _estimate(self, req: Request) -> int:
         """Footprint of a handle: measured for a shape seen before, else the GMRES work
         space (2m+4 vectors per system), the factors and the CG blocks."""
-        shape = (req.dim, req.m, req.N, req.P, self.params.get("precision"))
+        shape = self._shape(req)
         if shape in self.shape_bytes:
             return self.shape_bytes[shape]
         n = req.m ** req.dim
@@ -179,18 +215,18 @@ class OmmServer:
             threading.Thread(target=self._run, args=(req,), daemon=True).start()
 
     def _run(self, req: Request):
-        torch, omm = self.torch, self.omm
-        torch.cuda.set_device(self.device)
+        omm, dev = self.omm, self.dev
+        dev.set_device(self.device)
         t_start = time.perf_counter()
         res = self.resident.get(req.key)
         warm = res is not None and res.X is not None
         try:
             if res is None:
-                stream = torch.cuda.Stream()
-                with torch.cuda.stream(stream):
+                stream = dev.new_stream()
+                with dev.stream_ctx(stream):
                     prm = omm.default_params(**self.params)
                     s = omm.Solver(req.dim, req.m, req.L, req.V, req.N, shift=req.sigma, params=prm,
-                                   stream=stream.cuda_stream)
+                                   stream=dev.stream_handle(stream))
                     z, w = omm.poles_fermi(req.lam1, req.lamN, req.lamN1, req.P)
                     s.set_poles(z, w)
                 res = _Resident(s, s.device_bytes(), stream)
@@ -199,9 +235,9 @@ class OmmServer:
                     self.resident[req.key] = res
                     self.creating.discard(req.key)
                     self.reserved.pop(req.key, None)
-                    self.shape_bytes[(req.dim, req.m, req.N, req.P, self.params.get("precision"))] = res.bytes
+                    self.shape_bytes[self._shape(req)] = res.bytes
             s = res.solver
-            with torch.cuda.stream(res.stream):
+            with dev.stream_ctx(res.stream):
                 if warm:
                     s.set_orbitals(res.X)
                 else:
@@ -209,13 +245,11 @@ class OmmServer:
                     if X0 is None:
                         from workloads import gaussian_block   # seeded synthetic start
                         X0 = gaussian_block(s.n, s.N, seed=1000 + req.rid)
-                    Xd = torch.from_numpy(np.ascontiguousarray(X0)).to(device="cuda", dtype=s.dtype,
-                                                                       non_blocking=False)
-                    s.set_orbitals(Xd)
+                    s.set_orbitals(dev.upload(X0, s.dtype))
                 st = s.solve()
                 X = s.get_orbitals()
                 res.X = X
-                Xh = X.cpu().numpy()
+                Xh = dev.download(X)
             done = time.perf_counter()
             self.results.put(Result(req.rid, req.key, Xh, st, done - req.arrival, t_start - req.arrival, warm))
         finally:

@@ -92,7 +92,7 @@ typedef struct {
                            omm_set_poles returns OMM_EINVAL.  omm_set_orbitals drops the
                            imaginary part of the block.  0: complex X, P solves.       */
   int trsv_streams;     /* streams for the triangular solves, one group of poles each
-                           (1..4; 0 = 4).  Several let the latency-bound top of the
+                           (1..8; 0 = 8, one pole per stream for the folded 16-pole rule).  Several let the latency-bound top of the
                            elimination tree of one group overlap other groups' work; use
                            1 when many handles already run concurrently (serving).      */
 } omm_params;

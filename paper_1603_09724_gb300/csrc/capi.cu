@@ -67,7 +67,7 @@ struct omm_ctx {
   size_t csz = 16;
   cudaStream_t st = nullptr;
   // extra streams for the triangular solves of groups of poles (forked from and joined to st)
-  static constexpr int kTrsvStreams = 4;
+  static constexpr int kTrsvStreams = 8;
   cudaStream_t st2[kTrsvStreams] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kTrsvStreams] = {};
   void* (*alloc)(size_t, void*) = nullptr;

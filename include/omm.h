@@ -12,7 +12,8 @@
  * direct, lst): P R = sum_j w_j (H - sigma - z_j)^-1 R, each shifted system solved
  * roughly by restarted GMRES whose right preconditioner is the sparsifying
  * preconditioner of Sec. 3.2 (eqs. GLu, QG, P), set up once per pole on the host and
- * applied on the device by triangular solves.
+ * applied on the device by triangular solves.  Alternatively the preconditioner is the
+ * precomputed U U^* of Sec. 3.3, Algorithm 2 (omm_build_projector).
  *
  * Layout conventions
  *   - A grid function is n = m^d contiguous complex values, x index fastest
@@ -25,9 +26,11 @@
  * Ownership: inputs are copied or only read during the call; the handle owns all of its
  * device state and frees it in omm_destroy.  Device pointers passed in are borrowed
  * for the duration of the call.
- * Streams: every device operation is enqueued on the stream given to omm_create.  Calls
- * that return host values (energies, statistics) synchronise that stream; the others are
- * asynchronous with respect to the host.
+ * Streams: every device operation is ordered on the stream given to omm_create.  The
+ * triangular solves of different poles run on streams the handle owns (omm_params.
+ * trsv_streams), forked from and joined back to that stream with events inside each call.
+ * Calls that return host values (energies, statistics) synchronise that stream; the others
+ * are asynchronous with respect to the host.
  * Threads: a handle must not be used by two threads at once.  No C++ exception crosses
  * this interface; every call returns an omm_status.
  */
@@ -84,17 +87,19 @@ typedef struct {
   int gram_tensor;      /* 1: complex64 Grams on tcgen05 tensor cores (TF32 x 3 split,
                            FP64 split-K sum); 0: CUDA cores.  FP64 handles use CUDA cores */
   int real_orbitals;    /* 1: X is kept real (H is real symmetric with the symmetric
-                           kinetic symbol, and Sec. 3.1 writes the pole solutions real).  omm_set_poles then folds
-                           each conjugate pair (z, w), (conj z, conj w) into one solve:
+                           kinetic symbol, and Sec. 3.1 writes the pole solutions
+                           real).  omm_set_poles then folds each conjugate pair
+                           (z, w), (conj z, conj w) into one solve:
                            w Y + conj(w Y) = 2 Re(w Y) for real right-hand sides, so the
                            pole expansion costs P/2 GMRES solves; poles must come in
                            conjugate pairs (or be real with real weight), else
                            omm_set_poles returns OMM_EINVAL.  omm_set_orbitals drops the
                            imaginary part of the block.  0: complex X, P solves.       */
   int trsv_streams;     /* streams for the triangular solves, one group of poles each
-                           (1..8; 0 = 8, one pole per stream for the folded 16-pole rule).  Several let the latency-bound top of the
-                           elimination tree of one group overlap other groups' work; use
-                           1 when many handles already run concurrently (serving).      */
+                           (1..8; 0 = 8: one pole per stream for the folded 16-pole
+                           rule).  Several let the latency-bound top of the elimination
+                           tree of one group overlap the other groups' work; use 1 when
+                           many handles already run concurrently (serving).           */
 } omm_params;
 
 typedef struct {
@@ -126,7 +131,8 @@ omm_status omm_default_shift(const omm_grid* g, const double* V, double* shift);
 /* Create a handle.  V: host, n doubles, copied.  N: number of states (1 <= N < n).
  * shift: sigma; must exceed T_max + max V (else OMM_ESHIFT).  p: NULL for defaults.
  * stream: a cudaStream_t (NULL = legacy default stream).  Allocates the device work
- * space for the CG and for P_max = 32 poles' GMRES on the current device.
+ * space of the CG on the current device (the GMRES work space of the poles is allocated
+ * by omm_set_poles; at most 32 poles).
  * Errors: OMM_EINVAL, OMM_EUNSUPPORTED (grid), OMM_ESHIFT, OMM_ENOMEM, OMM_ECUDA. */
 omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, const omm_params* p,
                       void* stream, omm_t* out);
@@ -147,6 +153,8 @@ omm_status omm_poles_circle(double center, double radius, int P, double* z, doub
  * 2P doubles each; 1 <= P <= 32.  With the sparsifying inner preconditioner this builds,
  * for every pole, the stencil row q (SVD of G(a, a^c), eq. QG), the sparse matrix P_j
  * (eq. P), its nested-dissection multifrontal LU (host, FP64) and uploads the factors.
+ * With real_orbitals the conjugate pairs are folded first (see omm_params).  A projector
+ * built by omm_build_projector no longer applies after new poles and is dropped.
  * Errors: OMM_EINVAL, OMM_ENOMEM, OMM_ECUDA. */
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w);
 

@@ -402,14 +402,4 @@ cudaError_t launch_count_active(KrylovDims d, const int* active, int* nactive, c
   return cudaGetLastError();
 }
 
-__global__ void krylov_reset_kernel(KrylovDims d, int* active, int* steps) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < d.S) { active[s] = 1; steps[s] = 0; }
-}
-
-cudaError_t launch_krylov_reset(KrylovDims d, int* active, int* steps, cudaStream_t st) {
-  krylov_reset_kernel<<<(d.S + 255) / 256, 256, 0, st>>>(d, active, steps);
-  return cudaGetLastError();
-}
-
 }  // namespace omm

@@ -113,7 +113,5 @@ cudaError_t launch_count_active(KrylovDims d, const int* active, int* nactive, c
 // out = sign * sum_p w_p x_p over the P poles; real_part: out = (Re(...), 0)
 cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w, double sign, int real_part,
                                 const void* x, void* out, cudaStream_t st);
-// active[s] = 1 for all s; steps[s] = 0
-cudaError_t launch_krylov_reset(KrylovDims d, int* active, int* steps, cudaStream_t st);
 
 }  // namespace omm

@@ -19,6 +19,18 @@ def test_metrics_invariances():
     assert metrics.cond_number([1.0, 2.0, 4.0, 11.0], 2) == pytest.approx(10.0 / 2.0)
 
 
+def test_metrics_closed_form_for_two_lines():
+    """Two lines of R^2 at angle theta: the largest principal angle has sine |sin theta|,
+    and the projector difference [[-s^2, cs], [cs, s^2]] has largest entry max(s^2, |cs|)
+    (d is the entrywise-max ratio, the projector of the reference line has entry 1)."""
+    for th in (0.1, 0.7, 1.3):
+        c, s_ = np.cos(th), np.sin(th)
+        X0 = np.array([[1.0, 0.0]])
+        X = np.array([[c, s_]]) * 3.0                    # any scale: the span is what counts
+        assert metrics.max_angle_sine(X, X0) == pytest.approx(abs(s_), abs=1e-14)
+        assert metrics.d_metric(X, X0) == pytest.approx(max(s_ * s_, abs(c * s_)), abs=1e-14)
+
+
 def test_small_solve_reaches_the_eigenspace():
     """Filter + preconditioned CG with exact pole solves: E = 1/2 sum lam_i and the
     subspace angle to the eigh subspace below 1e-10 (one refilter removes the filter

@@ -18,6 +18,8 @@ Modules
   sparsify     sparsifying preconditioner (Sec. 3.2, eqs. GLu, QG, P)
   gmres        restarted right-preconditioned GMRES (Sec. 3.1 eq. lst, Sec. 4 params)
   precond      the preconditioner P = sum_j w_j (H - z_j)^-1 applied to a block
+  gtpa         Fourier-diagonal comparison preconditioners (Sec. 2.2, eqs. Lap, TPA,
+               gTPA) and their scale tau (Sec. 4)
   metrics      principal angles, d(X, X0) (Sec. 4), condition number (Sec. 2.3)
 
 Parity status: every function here is pinned by a -m "not gpu" test against a closed

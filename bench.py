@@ -36,9 +36,12 @@ def args_parse():
     ap.add_argument("--workload", default="smooth2d-128",
                     help="smooth2d-128 (the default line), wells2d-32, lattice3d-48")
     ap.add_argument("--gram-tensor", type=int, default=0, help="1: Grams on the tcgen05 tensor cores (TF32 x 3)")
-    ap.add_argument("--precond", default="pole", choices=["pole", "projector"],
+    ap.add_argument("--precond", default="pole", choices=["pole", "projector", "gtpa"],
                     help="pole: the pole expansion every iteration (Sec. 3.1); projector: U U^* precomputed by "
-                         "Algorithm 2 inside each timed solve (Sec. 3.3)")
+                         "Algorithm 2 inside each timed solve (Sec. 3.3); gtpa: the Fourier-diagonal TPA-type "
+                         "comparison preconditioner of Sec. 2.2 (no filter, tau from the exact eigenvectors)")
+    ap.add_argument("--gtpa-t", type=int, default=3, help="gtpa: polynomial degree t (3 = eq. TPA; the paper's gTPA runs use 5)")
+    ap.add_argument("--maxit", type=int, default=0, help="CG iteration cap (0: 40, or 4000 with gtpa as in Sec. 4)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass (profiler runs)")
     ap.add_argument("--inner", default="auto", choices=["auto", "spp", "kinetic"],
                     help="GMRES inner preconditioner; auto: sparsifying in 2D and up to 16^3, kinetic above")
@@ -185,6 +188,26 @@ def cpu_baseline_record(wl, spectra, applications):
                        f"SuperLU, BLAS pool {threads_used()} threads; cores = CPU time / wall time of the sample")}
 
 
+def cpu_baseline_gtpa(wl, spectra, t, iters, real=True, sample_iters=8):
+    """The oracle's OMM with the same gTPA preconditioner (Algorithm 1, FP64, pocketfft)
+    for a bounded number of iterations on the whole workload, scaled to the GPU solve's
+    iteration count."""
+    import numpy as np
+    from oracle import gtpa as ogtpa, hamiltonian as ham, omm as oomm
+    V = wl.potential_values()
+    pc = ogtpa.GtpaPreconditioner(wl.shape, ogtpa.default_coefficients(t), spectra["gtpa_tau"])
+    X0 = wl.initial_block(np.complex128, real=real)
+    t0, c0 = time.perf_counter(), time.process_time()
+    oomm.nlcg(lambda Y: ham.apply_h_fft(Y, wl.shape, wl.L, V, spectra["sigma"]), pc, X0, maxit=sample_iters, tol=0.0)
+    wall = time.perf_counter() - t0
+    cores = round(max((time.process_time() - c0) / wall, 1.0), 1)
+    per_solve = wall / sample_iters * max(iters, 1)
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle OMM with gTPA t = {t}: {sample_iters} iterations of Algorithm 1 on the whole "
+                       f"workload ({wall:.1f} s), scaled to the GPU solve's {iters} iterations; cores = CPU time / "
+                       f"wall time of the sample")}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -253,14 +276,19 @@ def run_ours(a):
     cdt = torch.complex64 if mixed else torch.complex128
     z, w = omm.poles_fermi(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
     tol = 0.0 if a.iters else (1e-10 if mixed else 1e-13)
-    maxit = a.iters if a.iters else 40
+    maxit = a.iters if a.iters else (a.maxit or (4000 if a.precond == "gtpa" else 40))
     real = a.orbitals == "real"
     inner = omm.OMM_INNER_SPARSIFY if inner_choice(wl, a.inner) == "spp" else omm.OMM_INNER_KINETIC
     prm = omm.default_params(precision=prec, maxit=maxit, tol=tol, refilter=a.refilter, gmres_rtol=a.rtol,
                              real_orbitals=int(real), inner=inner, gram_tensor=a.gram_tensor)
     s = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
     t_setup = time.perf_counter()
-    s.set_poles(z, w)
+    if a.precond == "gtpa":
+        if "gtpa_tau" not in spectra:
+            raise SystemExit(f"no stored tau for {a.workload} (2D workloads only)")
+        s.set_gtpa(a.gtpa_t, spectra["gtpa_tau"])
+    else:
+        s.set_poles(z, w)
     t_setup = time.perf_counter() - t_setup
     X0h = torch.from_numpy(wl.initial_block(np.complex64 if mixed else np.complex128, real=real)).pin_memory()
     X0 = X0h.to("cuda")
@@ -341,8 +369,7 @@ def run_ours(a):
            "vs_baseline": None, "dtype": "c64" if mixed else "c128", "data": "synthetic",
            "config": dict(workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64", a.refilter, a.rtol,
                                           a.orbitals, a.inner),
-                          preconditioner=("pole expansion every iteration (Sec. 3.1)" if a.precond == "pole" else
-                                          "U U^* from Algorithm 2 (k = N, rank-revealing column choice), built inside each timed solve")),
+                          preconditioner=precond_text(a, spectra)),
            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
            "solve": {"iters": st["iters"], "filters": st["filters"], "converged": st["converged"],
                      "energy_fp64": st["energy_fp64"], "resid_fp64": st["resid_fp64"],
@@ -373,8 +400,18 @@ def run_ours(a):
     if not a.no_fp64_check and world == 1:
         rec["accuracy_vs_fp64"] = fp64_compare(a, wl, spectra, s, omm, torch, V, z, w)
     if not a.no_cpu_baseline:
-        rec["cpu_baseline"] = cpu_baseline_record(wl, spectra, st["filters"] + st["iters"])
+        rec["cpu_baseline"] = (cpu_baseline_gtpa(wl, spectra, a.gtpa_t, st["iters"], real) if a.precond == "gtpa"
+                               else cpu_baseline_record(wl, spectra, st["filters"] + st["iters"]))
     print(json.dumps(rec))
+
+
+def precond_text(a, spectra):
+    if a.precond == "pole":
+        return "pole expansion every iteration (Sec. 3.1)"
+    if a.precond == "projector":
+        return "U U^* from Algorithm 2 (k = N, rank-revealing column choice), built inside each timed solve"
+    return (f"gTPA t = {a.gtpa_t} (Sec. 2.2; t = 3 is eq. TPA), tau = {spectra.get('gtpa_tau', 0):.6g} from the exact "
+            "eigenvectors (Sec. 4); CG from the unfiltered start")
 
 
 def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w):

@@ -13,7 +13,8 @@
  * roughly by restarted GMRES whose right preconditioner is the sparsifying
  * preconditioner of Sec. 3.2 (eqs. GLu, QG, P), set up once per pole on the host and
  * applied on the device by triangular solves.  Alternatively the preconditioner is the
- * precomputed U U^* of Sec. 3.3, Algorithm 2 (omm_build_projector).
+ * precomputed U U^* of Sec. 3.3, Algorithm 2 (omm_build_projector), or, for comparison,
+ * one of the Fourier-diagonal TPA-type preconditioners of Sec. 2.2 (omm_set_gtpa).
  *
  * Layout conventions
  *   - A grid function is n = m^d contiguous complex values, x index fastest
@@ -162,18 +163,20 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w);
 omm_status omm_set_orbitals(omm_t h, const void* X);
 omm_status omm_get_orbitals(omm_t h, void* X);
 
-/* Filter the orbitals once: X <- P X (Sec. 4: the starting guess is filtered).
+/* Filter the orbitals once: X <- P X (Sec. 4: the starting guess is filtered) with the pole
+ * expansion, or U U^* once a projector is built (never with gTPA).
  * Errors: OMM_ESTATE if no poles are set. */
 omm_status omm_filter(omm_t h);
 
 /* k steps of Algorithm 1 from the current X (restarting the CG: the first step uses the
  * steepest preconditioned direction).  st may be NULL.  Returns OMM_OK, or OMM_ESHIFT if
- * the quartic was not bounded below. */
+ * the quartic was not bounded below; OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_iterate(omm_t h, int k, omm_stats* st);
 
 /* Whole solve: filter, CG until the energy criterion or maxit, then refilter rounds,
- * then the FP64 energy and residual of the result.  Returns OMM_ENOTCONV (with st
- * filled) if maxit was reached in the last round. */
+ * then the FP64 energy and residual of the result (with gTPA set: one CG round from the
+ * given orbitals, no filter).  Returns OMM_ENOTCONV (with st filled) if maxit was reached
+ * in the last round; OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_solve(omm_t h, omm_stats* st);
 
 /* E_omm of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams). */
@@ -204,7 +207,7 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
 
 /* Pole-expansion preconditioner on N columns: Y = sum_j w_j Y_j with Y_j the GMRES
  * solution of (H - sigma - z_j) Y_j = R started from R (Sec. 3.1 eqs. direct, lst); with a
- * projector built (omm_build_projector), Y = U U^* R.
+ * projector built (omm_build_projector), Y = U U^* R; with gTPA set (omm_set_gtpa), Y = P_t R.
  * R, Y device blocks of N columns.  st may be NULL (fills the gmres_* fields). */
 omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
 
@@ -214,7 +217,7 @@ omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
  * pivoting, the Gram form of QR with column pivoting; then Cholesky QR; all in FP64, U
  * stored in the handle precision), and from then on the handle's preconditioner is U U^*
  * (omm_iterate, omm_filter, omm_solve, omm_pole_solve): one Gram U^* R and one block update
- * U (U^* R) per application instead of the pole solves.
+ * U (U^* R) per application instead of the pole solves.  Drops a gTPA preconditioner.
  * B: device, n x ncols, handle precision, a Gaussian block (real for real orbitals);
  * ncols = N (k = 0 extra columns, as in the paper's experiments) or 2N (k = N: the pivoting
  * then picks well-conditioned columns, which keeps the GMRES error of Y from being
@@ -227,6 +230,26 @@ omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st)
 /* Return to the pole-expansion preconditioner (frees nothing; U is kept until the next
  * omm_build_projector or omm_destroy). */
 omm_status omm_drop_projector(omm_t h);
+
+/* Fourier-diagonal comparison preconditioner of Sec. 2.2 (eqs. Lap, TPA, gTPA), the
+ * TPA-type preconditioners the experiments of Sec. 4 compare against: the plane-wave
+ * component k of R is multiplied by
+ *     g_t(s) = p_t(s) / (p_t(s) + c_{t+1} s^{t+1}),  p_t(s) = c_0 + c_1 s + ... + c_t s^t,
+ *     s = |k|^2 / tau, k the integer wave vector in [-m/2, m/2)^d.
+ * t = 0 with c = (1, 1) is eq. Lap; t = 3 with c = (27, 18, 12, 8, 16) is eq. TPA.
+ * c: host, t + 2 doubles (copied), all >= 0 with c_0 > 0 and c_{t+1} > 0; NULL selects
+ * c_k = 27 (2/3)^k (k <= t), c_{t+1} = 3 * 27 (2/3)^{t+1}, which is eq. TPA at t = 3 (the
+ * paper gives no coefficients for other t).  tau > 0: Sec. 4 takes the largest kinetic
+ * energy (1/2) sum_k |k|^2 |xhat_j(k)|^2 over the normalised exact eigenvectors.  0 <= t <= 16.
+ * While set, it is the handle's preconditioner (omm_iterate, omm_solve, omm_pole_solve; one
+ * fused FFT / multiply / inverse-FFT pass per application), ahead of a projector or the pole
+ * expansion, and omm_solve starts the CG from the orbitals as given (no filter step).
+ * omm_filter keeps filtering with the pole expansion or the projector.  Poles are not needed.
+ * Errors: OMM_EINVAL (t, c or tau out of range), OMM_ENOMEM, OMM_ECUDA. */
+omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau);
+
+/* Stop using the gTPA preconditioner (back to the projector or the pole expansion). */
+omm_status omm_drop_gtpa(omm_t h);
 
 /* Statistics of the sparsifying factor of pole j (host outputs, any may be NULL):
  * number of supernodes, factor entries (L + U), smallest |pivot| / largest |pivot|,

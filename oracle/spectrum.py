@@ -20,6 +20,23 @@ from .hamiltonian import kinetic_symbol
 
 
 def lowest_eigs_kspace(shape, L, V, shift, count, kc):
+    K, Hk = _kspace_matrix(shape, L, V, shift, kc)
+    lam = np.linalg.eigvalsh(Hk)
+    return lam[:count]
+
+
+def kinetic_tau_kspace(shape, L, V, shift, N, kc):
+    """tau of the TPA-type preconditioners (Sec. 4, Test 1): the largest (1/2) sum_k |k|^2
+    |xhat_j(k)|^2 over the N lowest eigenvectors, here taken in the plane-wave box (whose
+    eigenvectors are the Fourier coefficients xhat_j themselves, unit norm)."""
+    K, Hk = _kspace_matrix(shape, L, V, shift, kc)
+    _, C = np.linalg.eigh(Hk)
+    k2 = np.sum(K.astype(np.float64) ** 2, axis=1)
+    return float(np.max(0.5 * (k2 @ (np.abs(C[:, :N]) ** 2))))
+
+
+def _kspace_matrix(shape, L, V, shift, kc):
+    """Integer wave vectors K of the box |k|_inf <= kc and H(k, k') restricted to it."""
     d = len(shape)
     m = shape[0]
     n = int(np.prod(shape))
@@ -34,8 +51,7 @@ def lowest_eigs_kspace(shape, L, V, shift, count, kc):
     diff = (K[:, None, :] - K[None, :, :])
     didx = tuple((diff[..., a] % shape[a]) for a in range(d))[::-1]
     Hk = Vh[didx] + np.diag(Tk) - shift * np.eye(len(ks))
-    lam = np.linalg.eigvalsh(Hk)
-    return lam[:count]
+    return K, Hk
 
 
 def lowest_eigs_bloch(shape, L, V, shift, cells, count):

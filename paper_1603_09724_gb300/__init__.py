@@ -61,6 +61,8 @@ _SIGS = {
     "omm_set_orbitals": (C.c_int, [_vp, _vp]),
     "omm_build_projector": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(omm_stats)]),
     "omm_drop_projector": (C.c_int, [_vp]),
+    "omm_set_gtpa": (C.c_int, [_vp, C.c_int, _dp, C.c_double]),
+    "omm_drop_gtpa": (C.c_int, [_vp]),
     "omm_get_orbitals": (C.c_int, [_vp, _vp]),
     "omm_filter": (C.c_int, [_vp]),
     "omm_iterate": (C.c_int, [_vp, C.c_int, C.POINTER(omm_stats)]),
@@ -289,6 +291,20 @@ class Solver:
 
     def drop_projector(self):
         check(lib.omm_drop_projector(self.h), "omm_drop_projector")
+
+    def set_gtpa(self, t, tau, coeffs=None):
+        """Fourier-diagonal TPA-type preconditioner (Sec. 2.2, eqs. Lap, TPA, gTPA) of degree t
+        with s = |k|^2 / tau; coeffs: c_0..c_{t+1} (None: the library's default family, eq. TPA
+        at t = 3).  While set it replaces the pole expansion and solve() does not filter."""
+        c = None
+        if coeffs is not None:
+            if len(coeffs) != t + 2:
+                raise ValueError("coeffs needs t + 2 values")
+            c = (C.c_double * (t + 2))(*[float(v) for v in coeffs])
+        check(lib.omm_set_gtpa(self.h, int(t), c, float(tau)), "omm_set_gtpa")
+
+    def drop_gtpa(self):
+        check(lib.omm_drop_gtpa(self.h), "omm_drop_gtpa")
 
     def factor_info(self, pole):
         ns, nnz, pr, npt = C.c_int(), C.c_longlong(), C.c_double(), C.c_int()

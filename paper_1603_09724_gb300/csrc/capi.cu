@@ -129,6 +129,10 @@ struct omm_ctx {
   void* projZero64 = nullptr;   // N x N complex128 zeros
   void* projWork64 = nullptr;   // FP64 Gram work
   bool poles_set = false;
+  // Fourier-diagonal comparison preconditioner (gTPA, Sec. 2.2)
+  bool use_gtpa = false;
+  void* gtpa_tab = nullptr;     // 2 x n working precision: +g_t(s_k)/n, then -g_t(s_k)/n
+  void* gtpa_one = nullptr;     // the one-point stencil {1} of the Green kernel
   // GMRES work (sized for P poles)
   int Palloc = 0;
   void* Vb = nullptr;
@@ -679,8 +683,23 @@ omm_status apply_projector(omm_ctx* h, const void* R, void* out, double sign) {
   return OMM_OK;
 }
 
-// The preconditioner of the handle: U U^* once built, else the pole expansion
+// out = sign * F^-1 (g_t(|k|^2 / tau) F R): one fused pass of the Green kernel with the
+// gTPA table (1/n folded in) and the one-point stencil; real orbitals drop the rounding
+// imaginary parts, as the pole sum does
+omm_status apply_gtpa(omm_ctx* h, const void* R, void* out, double sign) {
+  const void* tab = (const char*)h->gtpa_tab + (sign < 0 ? (size_t)h->n * h->csz : 0);
+  OMM_TRY(greenq(h, R, out, h->N, 1, h->N, nullptr, tab, h->gtpa_one));
+  if (h->prm.real_orbitals) {
+    const size_t cnt = (size_t)h->N * h->n;
+    PROF(PC_VEC, 1.0 * cnt * h->csz, 1, cuda_status(launch_real_part(h->dbl, cnt, out, h->st), "real"));
+  }
+  return OMM_OK;
+}
+
+// The preconditioner of the handle: gTPA while set, else U U^* once built, else the pole
+// expansion
 omm_status precondition(omm_ctx* h, const void* R, void* out, double sign) {
+  if (h->use_gtpa) return apply_gtpa(h, R, out, sign);
   if (h->use_proj) return apply_projector(h, R, out, sign);
   return pole_solve(h, R, out, sign);
 }
@@ -730,7 +749,7 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
          cuda_status(launch_axpby(h->dbl, cnt, &h->sc->t_c, h->HD(), &h->sc->one_c, h->HX(), h->st), "upd"));
     std::swap(h->G, h->Gp);
     OMM_TRY(read_scalars(h));
-    if (!h->use_proj) {
+    if (!h->use_proj && !h->use_gtpa) {
       OMM_TRY(gmres_stats(h));
       h->gmres_total += h->last_gmres_max;
     }
@@ -1211,13 +1230,13 @@ omm_status omm_get_orbitals(omm_t h, void* X) {
 omm_status omm_filter(omm_t h) {
   if (!h) return OMM_EINVAL;
   if (!h->poles_set) return OMM_ESTATE;
-  OMM_TRY(precondition(h, h->X(), h->G, +1.0));
+  OMM_TRY(h->use_proj ? apply_projector(h, h->X(), h->G, +1.0) : pole_solve(h, h->X(), h->G, +1.0));
   return cuda_status(cudaMemcpyAsync(h->X(), h->G, (size_t)h->N * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "copy");
 }
 
 omm_status omm_iterate(omm_t h, int k, omm_stats* st) {
   if (!h || k < 0) return OMM_EINVAL;
-  if (!h->poles_set) return OMM_ESTATE;
+  if (!h->poles_set && !h->use_gtpa) return OMM_ESTATE;
   if (st) std::memset(st, 0, sizeof(*st));
   h->gmres_total = 0;
   int done = 0;
@@ -1232,15 +1251,20 @@ omm_status omm_iterate(omm_t h, int k, omm_stats* st) {
 
 omm_status omm_solve(omm_t h, omm_stats* st) {
   if (!h) return OMM_EINVAL;
-  if (!h->poles_set) return OMM_ESTATE;
+  if (!h->poles_set && !h->use_gtpa) return OMM_ESTATE;
   omm_stats loc;
   std::memset(&loc, 0, sizeof(loc));
   h->gmres_total = 0;
   int total = 0;
   bool conv = false;
-  for (int round = 0; round <= h->prm.refilter; ++round) {
-    OMM_TRY(omm_filter(h));
-    loc.filters++;
+  // gTPA is no spectral filter: one CG round from the orbitals as given (Sec. 4's runs
+  // of the TPA-type preconditioners start from the initial guess)
+  const int rounds = h->use_gtpa ? 0 : h->prm.refilter;
+  for (int round = 0; round <= rounds; ++round) {
+    if (!h->use_gtpa) {
+      OMM_TRY(omm_filter(h));
+      loc.filters++;
+    }
     int done = 0;
     OMM_TRY(cg_steps(h, h->prm.maxit, &loc, &done, &conv));
     total += done;
@@ -1333,13 +1357,15 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
 
 omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st) {
   if (!h || !R || !Y) return OMM_EINVAL;
-  if (!h->poles_set) return OMM_ESTATE;
+  if (!h->poles_set && !h->use_gtpa) return OMM_ESTATE;
   OMM_TRY(precondition(h, R, Y, 1.0));
-  if (!h->use_proj) OMM_TRY(gmres_stats(h));
+  if (!h->use_proj && !h->use_gtpa) OMM_TRY(gmres_stats(h));
   if (st) {
     std::memset(st, 0, sizeof(*st));
-    st->gmres_iters_max = h->last_gmres_max;
-    st->gmres_relres_max = h->last_relres_max;
+    if (!h->use_gtpa) {
+      st->gmres_iters_max = h->last_gmres_max;
+      st->gmres_relres_max = h->last_relres_max;
+    }
   }
   return OMM_OK;
 }
@@ -1519,12 +1545,62 @@ omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st)
   else
     PROF(PC_VEC, 24.0 * cnt, 1, cuda_status(launch_convert(false, cnt, Y64, h->Uproj, h->st), "convert"));
   h->use_proj = true;
+  h->use_gtpa = false;
   return OMM_OK;
 }
 
 omm_status omm_drop_projector(omm_t h) {
   if (!h) return OMM_EINVAL;
   h->use_proj = false;
+  return OMM_OK;
+}
+
+omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau) {
+  if (!h || t < 0 || t > 16 || !(tau > 0.0) || !std::isfinite(tau)) return OMM_EINVAL;
+  std::vector<double> cc(t + 2);
+  if (c) {
+    for (int k = 0; k < t + 2; ++k) {
+      if (!std::isfinite(c[k]) || c[k] < 0.0) return OMM_EINVAL;
+      cc[k] = c[k];
+    }
+    if (!(cc[0] > 0.0) || !(cc[t + 1] > 0.0)) return OMM_EINVAL;
+  } else {
+    // c_k = 27 (2/3)^k for k <= t and c_{t+1} = 3 * 27 (2/3)^{t+1}: eq. TPA at t = 3
+    for (int k = 0; k <= t; ++k) cc[k] = 27.0 * std::pow(2.0 / 3.0, k);
+    cc[t + 1] = 3.0 * 27.0 * std::pow(2.0 / 3.0, t + 1);
+  }
+  const size_t n = h->n;
+  const int m = h->m;
+  std::vector<cd> tab(2 * n);
+  auto sk = [m](int i) { return i < m / 2 ? i : i - m; };
+  for (size_t i = 0; i < n; ++i) {
+    const int ix = (int)(i % m), iy = (int)((i / m) % m), iz = h->dim == 3 ? (int)(i / ((size_t)m * m)) : 0;
+    const double k2 = (double)sk(ix) * sk(ix) + (double)sk(iy) * sk(iy) + (h->dim == 3 ? (double)sk(iz) * sk(iz) : 0.0);
+    const double s = k2 / tau;
+    double p = cc[t], st = s;            // Horner for p_t(s); s^{t+1} alongside
+    for (int k = t - 1; k >= 0; --k) {
+      p = p * s + cc[k];
+      st *= s;
+    }
+    double g = p / (p + cc[t + 1] * st);
+    if (!std::isfinite(g)) g = 0.0;      // s^{t+1} and p_t both overflowed: the limit s -> inf
+    tab[i] = cd(g / (double)n, 0.0);
+    tab[n + i] = cd(-g / (double)n, 0.0);
+  }
+  if (!h->gtpa_one) {
+    OMM_TRY(h->dalloc(&h->gtpa_one, h->csz));
+    OMM_TRY(upload_complex(h, h->gtpa_one, std::vector<cd>(1, cd(1.0, 0.0)), h->dbl));
+  }
+  if (!h->gtpa_tab) OMM_TRY(h->dalloc(&h->gtpa_tab, 2 * n * h->csz));
+  OMM_TRY(upload_complex(h, h->gtpa_tab, tab, h->dbl));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "gtpa sync"));
+  h->use_gtpa = true;
+  return OMM_OK;
+}
+
+omm_status omm_drop_gtpa(omm_t h) {
+  if (!h) return OMM_EINVAL;
+  h->use_gtpa = false;
   return OMM_OK;
 }
 

@@ -110,3 +110,24 @@ def test_omm_with_tpa_reaches_the_energy_in_many_more_iterations(scale):
     _, hist = oomm.nlcg(H, pp, pp(X0), maxit=100, tol=1e-13)
     assert hist[-1]["E"] == pytest.approx(Eref, rel=1e-10)
     assert min(iters.values()) > 8 * (len(hist) - 1), (iters, len(hist) - 1)
+
+
+def test_tau_from_the_plane_wave_box_matches_the_dense_route():
+    """oracle.spectrum.kinetic_tau_kspace (eigenvectors of H(k, k') in the plane-wave box,
+    used for grids too large for a dense eigh) equals kinetic_tau of the dense eigenvectors
+    when the box is the whole grid, and converges as the box grows for a smooth field."""
+    from oracle import spectrum
+    from workloads import smooth_field_2d
+    m, N, L = 12, 5, 10.0
+    V = wells_2d(m, L, seed=2)
+    sig = ham.default_shift((m, m), L, V)
+    _, U = np.linalg.eigh(ham.dense_h((m, m), L, V, sig))
+    dense = gtpa.kinetic_tau(U[:, :N].T, (m, m))
+    assert spectrum.kinetic_tau_kspace((m, m), L, V, sig, N, m // 2) == pytest.approx(dense, rel=1e-10)
+    m, N = 32, 12
+    V = smooth_field_2d(m, seed=3)
+    sig = ham.default_shift((m, m), L, V)
+    _, U = np.linalg.eigh(ham.dense_h((m, m), L, V, sig))
+    dense = gtpa.kinetic_tau(U[:, :N].T, (m, m))
+    errs = [abs(spectrum.kinetic_tau_kspace((m, m), L, V, sig, N, kc) / dense - 1) for kc in (8, 10, 12, 14)]
+    assert all(a > 10 * b for a, b in zip(errs, errs[1:])) and errs[-1] < 1e-6, errs

@@ -4,7 +4,9 @@ oracle.spectrum for the smooth 2D field and the exact Bloch sectors for the 3D l
 
 The pole rule needs the occupied interval [lam_1, lam_N] and lam_{N+1}; the paper builds
 its contour from the exact spectrum (Sec. 4), so the workloads carry these stored
-values.  E_ref = 1/2 sum_{i<=N} lam_i is the exact minimum of E_omm (Sec. 1).
+values.  E_ref = 1/2 sum_{i<=N} lam_i is the exact minimum of E_omm (Sec. 1).  gtpa_tau
+(2D workloads) is the scale tau of the TPA-type comparison preconditioners, which Sec. 4
+also takes from the exact eigenvectors.
 
 Run: python -m workloads.make_spectra
 """
@@ -15,7 +17,7 @@ import os
 
 import numpy as np
 
-from oracle import hamiltonian as ham
+from oracle import gtpa, hamiltonian as ham
 from oracle import spectrum
 from workloads import WORKLOADS, batch_mix, serving_mix
 
@@ -39,6 +41,17 @@ def compute(wl, kc=24):
     return dict(sigma=sig, lam1=float(lam[0]), lamN=float(lam[wl.N - 1]), lamN1=float(lam[wl.N]),
                 weyl_lo=lo, weyl_hi=hi, E_ref=float(0.5 * np.sum(lam[: wl.N])), method=how,
                 lowest=[float(x) for x in lam])
+
+
+def gtpa_tau(wl, sig, kc=24):
+    """tau of the TPA-type comparison preconditioners (Sec. 4): the largest kinetic energy
+    (1/2) sum_k |k|^2 |xhat_j(k)|^2 over the N exact lowest eigenvectors (dense eigh for
+    n <= 4096, else the plane-wave box).  2D workloads only."""
+    V = wl.potential_values()
+    if wl.n <= 4096:
+        _, U = np.linalg.eigh(ham.dense_h(wl.shape, wl.L, V, sig))
+        return gtpa.kinetic_tau(U[:, : wl.N].T, wl.shape)
+    return spectrum.kinetic_tau_kspace(wl.shape, wl.L, V, sig, wl.N, kc)
 
 
 def compute_spec(h, kc=24, window=8):
@@ -69,6 +82,11 @@ def main(names=("wells2d-32", "smooth2d-128", "lattice3d-48")):
             continue
         data[name] = compute(WORKLOADS[name])
         print(name, data[name]["lamN1"] - data[name]["lamN"], data[name]["method"])
+    for name in names:
+        wl = WORKLOADS[name]
+        if wl.dim == 2 and "gtpa_tau" not in data[name]:
+            data[name]["gtpa_tau"] = gtpa_tau(wl, data[name]["sigma"])
+            print(name, "tau", data[name]["gtpa_tau"])
     for h in batch_mix() + serving_mix():
         if h.key not in data:
             data[h.key] = compute_spec(h)

@@ -80,12 +80,16 @@ def test_iterations_follow_the_oracle(omm):
 @pytest.mark.parametrize("scale", [0.01, 1.0])
 def test_tpa_solve_reaches_the_energy_in_many_more_iterations(omm, scale):
     """Sec. 4: OMM with TPA converges to the exact energy, in many times the iterations
-    of the pole expansion (which here runs on the same handle after omm_drop_gtpa)."""
+    of the pole expansion (which here runs on the same handle after omm_drop_gtpa).  The
+    full-depth wells leave a gap of 0.012 in a spread of 30, so one filter with 16 poles
+    leaves leakage that stalls the pole-expansion CG at E error 4.3e-9 (the oracle stops at
+    the same value, exact pole solves included); one refilter round removes it.  The gTPA
+    solve does not filter, so the refilter setting does not touch it."""
     m, N, L = 16, 5, 10.0
     V, sig, lam, tau = small_case(m, N, L, scale)
     Eref = 0.5 * lam[:N].sum()
     X0 = to_dev(torch, gaussian_block_real(m * m, N, seed=7), torch.complex128)
-    p = omm.default_params(precision=0, maxit=3000, tol=1e-13, real_orbitals=1)
+    p = omm.default_params(precision=0, maxit=3000, tol=1e-13, real_orbitals=1, refilter=1)
     s = omm.Solver(2, m, L, V, N, shift=sig, params=p)
     z, w = opoles.poles_conformal(lam[0], lam[N - 1], lam[N], 16)
     s.set_poles(z, w)
@@ -97,7 +101,7 @@ def test_tpa_solve_reaches_the_energy_in_many_more_iterations(omm, scale):
     s.drop_gtpa()
     s.set_orbitals(X0)
     st_pole = s.solve()
-    assert st_pole["converged"] == 1 and st_pole["filters"] == 1
+    assert st_pole["converged"] == 1 and st_pole["filters"] == 2
     assert st_pole["energy_fp64"] == pytest.approx(Eref, rel=1e-10)
     assert st_tpa["iters"] > 8 * st_pole["iters"], (st_tpa["iters"], st_pole["iters"])
     s.close()

@@ -198,6 +198,66 @@ void one_sided_jacobi(std::vector<cd>& B, int rows, int cols, std::vector<cd>& V
   }
 }
 
+// y[0..len) -= a x[0..len) on the interleaved (re, im) doubles of std::complex arrays: a
+// plain loop that compilers vectorise (std::complex products keep a scalar inf/nan path)
+inline void caxpy_sub(int len, cd a, const cd* x, cd* y) {
+  const double ar = a.real(), ai = a.imag();
+  const double* xd = reinterpret_cast<const double*>(x);
+  double* yd = reinterpret_cast<double*>(y);
+  for (int j = 0; j < len; ++j) {
+    const double xr = xd[2 * j], xi = xd[2 * j + 1];
+    yd[2 * j] -= ar * xr - ai * xi;
+    yd[2 * j + 1] -= ar * xi + ai * xr;
+  }
+}
+
+// Partial LU without pivoting of the first ns rows / columns of the nf x nf row-major
+// front F: on return F holds the unit-lower multipliers, U, and in its trailing
+// (nf - ns)^2 block the Schur complement.  Blocked right-looking elimination: inside a
+// panel of kPanel pivots each pivot row is first brought fully up to date (its part
+// beyond the panel receives the panel's earlier pivots), so every pivot sees its whole
+// updated row exactly as in unblocked elimination; then the rows below the panel get the
+// panel's rank-kPanel update one row at a time, with the panel's rows of U in cache.
+// Rows and terms with a zero multiplier are skipped.  A pivot below pivot_floor times the
+// largest entry of its updated row is raised to that size (static pivoting) and counted.
+void partial_lu(cd* F, int nf, int ns, double pivot_floor, SppPole& out) {
+  constexpr int kPanel = 32;
+  const cd zero(0.0, 0.0);
+  for (int kb = 0; kb < ns; kb += kPanel) {
+    const int ke = std::min(kb + kPanel, ns);
+    for (int k = kb; k < ke; ++k) {
+      cd* rk = F + (size_t)k * nf;
+      for (int p = kb; p < k; ++p)
+        if (rk[p] != zero) caxpy_sub(nf - ke, rk[p], F + (size_t)p * nf + ke, rk + ke);
+      cd piv = rk[k];
+      double rown = 0.0;
+      for (int j = k; j < nf; ++j) rown = std::max(rown, std::abs(rk[j]));
+      const double ap = std::abs(piv);
+      if (ap < pivot_floor * rown || ap == 0.0) {
+        const double mag = pivot_floor * (rown > 0.0 ? rown : 1.0);
+        piv = (ap > 0.0) ? piv / ap * mag : cd(mag, 0.0);
+        rk[k] = piv;
+        ++out.nperturbed;
+      }
+      out.pivot_min = std::min(out.pivot_min, std::abs(piv));
+      out.pivot_max = std::max(out.pivot_max, std::abs(piv));
+      const cd ip = 1.0 / piv;
+      for (int i = k + 1; i < nf; ++i) {
+        cd* ri = F + (size_t)i * nf;
+        if (ri[k] == zero) continue;
+        const cd l = ri[k] * ip;
+        ri[k] = l;
+        caxpy_sub(ke - k - 1, l, rk + k + 1, ri + k + 1);   // the panel's columns only
+      }
+    }
+    for (int i = ke; i < nf; ++i) {                          // F22 -= L21 U12
+      cd* ri = F + (size_t)i * nf;
+      for (int p = kb; p < ke; ++p)
+        if (ri[p] != zero) caxpy_sub(nf - ke, ri[p], F + (size_t)p * nf + ke, ri + ke);
+    }
+  }
+}
+
 }  // namespace
 
 SppStructure spp_build_structure(int dim, int m, int r) {
@@ -483,67 +543,45 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
     const bool leaf = children[s].empty() && !st.leaf_nodes.empty();   // banded leaf data (2D) is kept
     std::vector<cd> F0;
     if (leaf) F0 = F;   // original couplings of the leaf (no children: F holds only P's entries)
-    // partial LU of the first ns rows / columns
-    for (int k = 0; k < ns; ++k) {
-      cd piv = F[(size_t)k * nf + k];
-      double rown = 0.0;
-      for (int j = k; j < nf; ++j) rown = std::max(rown, std::abs(F[(size_t)k * nf + j]));
-      const double ap = std::abs(piv);
-      if (ap < pivot_floor * rown || ap == 0.0) {
-        const double mag = pivot_floor * (rown > 0.0 ? rown : 1.0);
-        piv = (ap > 0.0) ? piv / ap * mag : cd(mag, 0.0);
-        F[(size_t)k * nf + k] = piv;
-        ++out.nperturbed;
-      }
-      out.pivot_min = std::min(out.pivot_min, std::abs(piv));
-      out.pivot_max = std::max(out.pivot_max, std::abs(piv));
-      const cd ip = 1.0 / piv;
-      const cd* rk = &F[(size_t)k * nf];
-      for (int i = k + 1; i < nf; ++i) {
-        cd* ri = &F[(size_t)i * nf];
-        if (ri[k] == cd(0.0, 0.0)) continue;
-        const cd l = ri[k] * ip;
-        ri[k] = l;
-        for (int j = k + 1; j < nf; ++j) ri[j] -= l * rk[j];
-      }
-    }
+    partial_lu(F.data(), nf, ns, pivot_floor, out);
     // W_f = [L_SS^-1 ; L_BS L_SS^-1], W_b = [U_SS^-1 , -U_SS^-1 U_SB]: with these, each
-    // supernode's forward and backward step is one dense product on the device
-    std::vector<cd> Li((size_t)ns * ns, cd(0.0, 0.0)), Ui((size_t)ns * ns, cd(0.0, 0.0));
-    for (int c = 0; c < ns; ++c) {           // L Li = I, L unit lower (multipliers in F)
-      Li[(size_t)c * ns + c] = 1.0;
-      for (int i = c + 1; i < ns; ++i) {
-        cd acc(0.0, 0.0);
-        for (int k = c; k < i; ++k) acc += F[(size_t)i * nf + k] * Li[(size_t)k * ns + c];
-        Li[(size_t)i * ns + c] = -acc;
-      }
+    // supernode's forward and backward step is one dense product on the device.  All four
+    // are formed row by row from contiguous rows (zero coefficients skipped).
+    const cd zero(0.0, 0.0);
+    std::vector<cd> Li((size_t)ns * ns, zero), Ui((size_t)ns * ns, zero);
+    for (int i = 0; i < ns; ++i) {           // L Li = I: Li(i,:) = e_i - sum_{k<i} L(i,k) Li(k,:)
+      cd* li = &Li[(size_t)i * ns];
+      li[i] = 1.0;
+      const cd* lrow = &F[(size_t)i * nf];
+      for (int k = 0; k < i; ++k)
+        if (lrow[k] != zero) caxpy_sub(k + 1, lrow[k], &Li[(size_t)k * ns], li);
     }
-    for (int c = ns - 1; c >= 0; --c) {      // U Ui = I, U upper (diagonal = pivots)
-      Ui[(size_t)c * ns + c] = 1.0 / F[(size_t)c * nf + c];
-      for (int i = c - 1; i >= 0; --i) {
-        cd acc(0.0, 0.0);
-        for (int k = i + 1; k <= c; ++k) acc += F[(size_t)i * nf + k] * Ui[(size_t)k * ns + c];
-        Ui[(size_t)i * ns + c] = -acc / F[(size_t)i * nf + i];
-      }
+    for (int i = ns - 1; i >= 0; --i) {      // U Ui = I: Ui(i,:) = (e_i - sum_{k>i} U(i,k) Ui(k,:)) / U(i,i)
+      cd* ui = &Ui[(size_t)i * ns];
+      ui[i] = 1.0;
+      const cd* urow = &F[(size_t)i * nf];
+      for (int k = i + 1; k < ns; ++k)
+        if (urow[k] != zero) caxpy_sub(ns - k, urow[k], &Ui[(size_t)k * ns + k], ui + k);
+      const cd d = 1.0 / urow[i];
+      for (int j = i; j < ns; ++j) ui[j] *= d;
     }
     cd* wf = &out.factor[nd.wf];
     cd* wb = &out.factor[nd.wb];
-    for (int i = 0; i < ns; ++i)
-      for (int j = 0; j < ns; ++j) wf[(size_t)i * ns + j] = Li[(size_t)i * ns + j];
-    for (int i = 0; i < nb; ++i)
-      for (int j = 0; j < ns; ++j) {
-        cd acc(0.0, 0.0);
-        for (int k = j; k < ns; ++k) acc += F[(size_t)(ns + i) * nf + k] * Li[(size_t)k * ns + j];
-        wf[(size_t)(ns + i) * ns + j] = acc;
-      }
+    std::copy(Li.begin(), Li.end(), wf);
+    for (int i = 0; i < nb; ++i) {           // L_BS Li
+      cd* w = wf + (size_t)(ns + i) * ns;
+      std::fill(w, w + ns, zero);
+      const cd* lrow = &F[(size_t)(ns + i) * nf];
+      for (int k = 0; k < ns; ++k)
+        if (lrow[k] != zero) caxpy_sub(k + 1, -lrow[k], &Li[(size_t)k * ns], w);
+    }
     const int kb = ns + nb;
-    for (int i = 0; i < ns; ++i) {
-      for (int j = 0; j < ns; ++j) wb[(size_t)i * kb + j] = Ui[(size_t)i * ns + j];
-      for (int j = 0; j < nb; ++j) {
-        cd acc(0.0, 0.0);
-        for (int k = i; k < ns; ++k) acc += Ui[(size_t)i * ns + k] * F[(size_t)k * nf + ns + j];
-        wb[(size_t)i * kb + ns + j] = -acc;
-      }
+    for (int i = 0; i < ns; ++i) {           // [Ui , -Ui U_SB]
+      cd* w = wb + (size_t)i * kb;
+      std::copy(&Ui[(size_t)i * ns], &Ui[(size_t)i * ns] + ns, w);
+      std::fill(w + ns, w + kb, zero);
+      for (int k = i; k < ns; ++k)
+        if (w[k] != zero) caxpy_sub(nb, w[k], &F[(size_t)k * nf + ns], w + ns);
     }
     if (leaf) {
       const int bw = st.leaf_bw, NB = SppStructure::NBR;

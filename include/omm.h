@@ -133,7 +133,9 @@ omm_status omm_default_shift(const omm_grid* g, const double* V, double* shift);
  * shift: sigma; must exceed T_max + max V (else OMM_ESHIFT).  p: NULL for defaults.
  * stream: a cudaStream_t (NULL = legacy default stream).  Allocates the device work
  * space of the CG on the current device (the GMRES work space of the poles is allocated
- * by omm_set_poles; at most 32 poles).
+ * by omm_set_poles; at most 32 poles).  All arguments are checked on the host before any
+ * device work: OMM_EINVAL for a non-finite V or shift, NaN or negative tolerances or pivot
+ * floor, or other parameters out of range.
  * Errors: OMM_EINVAL, OMM_EUNSUPPORTED (grid), OMM_ESHIFT, OMM_ENOMEM, OMM_ECUDA. */
 omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, const omm_params* p,
                       void* stream, omm_t* out);

@@ -1012,7 +1012,9 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
   if (p) prm = *p;
   if (prm.gmres_m < 1 || prm.gmres_m > 15 || prm.gmres_cycles < 1 || prm.maxit < 0 || prm.refilter < 0 ||
       (prm.precision != OMM_FP64 && prm.precision != OMM_MIXED) || prm.inner < 0 || prm.inner > 2 ||
-      prm.stencil_radius != 1 || prm.trsv_streams < 0 || prm.trsv_streams > omm_ctx::kTrsvStreams)
+      prm.stencil_radius != 1 || prm.trsv_streams < 0 || prm.trsv_streams > omm_ctx::kTrsvStreams ||
+      !(prm.gmres_rtol >= 0.0) || !std::isfinite(prm.gmres_rtol) || !(prm.tol >= 0.0) || !std::isfinite(prm.tol) ||
+      !(prm.pivot_floor >= 0.0) || !std::isfinite(prm.pivot_floor) || !std::isfinite(shift))
     return OMM_EINVAL;
   const bool dbl = prm.precision == OMM_FP64;
   if (!fused_fft_supported(g->dim, m, dbl) && !big_fft_supported(g->dim, m)) return OMM_EUNSUPPORTED;

@@ -72,3 +72,32 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     assert create(g, 2 * tmax, bad) == omm.OMM_EINVAL
     assert create(g, 2 * tmax, None, Np=0) == omm.OMM_EINVAL
     assert not h.value
+
+
+def test_create_rejects_non_finite_inputs_before_touching_the_device():
+    """Injected faults, caught on the host: a NaN or an infinity in V, a non-finite shift,
+    NaN or negative tolerances and pivot floor all return OMM_EINVAL and leave no handle."""
+    import ctypes as C
+    import numpy as np
+    import paper_1603_09724_gb300 as omm
+    m, L = 16, 10.0
+    g = omm.make_grid(2, m, L)
+    shift = 2 * (2 * np.pi ** 2 / L ** 2 * 2 * (m // 2) ** 2)
+    h = C.c_void_p()
+
+    def create(V, shift, prm=None):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        return omm.lib.omm_create(C.byref(g), V.ctypes.data_as(C.POINTER(C.c_double)), 4, shift,
+                                  C.byref(prm) if prm is not None else None, None, C.byref(h))
+
+    for bad in (np.nan, np.inf, -np.inf):
+        V = np.zeros(m * m)
+        V[37] = bad
+        assert create(V, shift) == omm.OMM_EINVAL
+    V = np.zeros(m * m)
+    for s in (np.nan, np.inf):
+        assert create(V, s) == omm.OMM_EINVAL
+    for kw in (dict(gmres_rtol=np.nan), dict(gmres_rtol=-1e-5), dict(tol=np.nan), dict(tol=-1.0),
+               dict(pivot_floor=np.nan), dict(pivot_floor=-1e-12), dict(tol=np.inf)):
+        assert create(V, shift, omm.default_params(**kw)) == omm.OMM_EINVAL, kw
+    assert not h.value

@@ -2,7 +2,8 @@
 //
 //   G = (T + l - sigma - z)^-1 with l = <V> (eq. GLu), a circulant: G(i, j) = g[i - j]
 //   Q(j, a(j)) = q for every j: q = conj(u_min), u_min the left singular vector of
-//     G(a, a^c) for its smallest singular value (one-sided Jacobi SVD of G(a, a^c)^*) (eq. QG)
+//     G(a, a^c) for its smallest singular value (Householder QR of G(a, a^c)^*, then a
+//     one-sided Jacobi SVD of its R) (eq. QG)
 //   P_{j, j+o} = q_o + (qG)_o (V_{j+o} - l) on the stencil, 0 elsewhere (eq. P)
 //   P = L U by nested dissection (recursive bisection of the periodic grid by grid
 //   lines / planes) and a multifrontal factorisation with dense fronts, no pivoting
@@ -151,6 +152,37 @@ void idft_separable(int dim, int m, std::vector<cd>& a) {
       }
       for (int t = 0; t < m; ++t) a[base + t * stride] = res[t];
     }
+  }
+}
+
+// R factor (cols x cols, column-major, upper triangular) of the Householder QR of B (rows x
+// cols, column-major, overwritten by the reflectors): B = Q R, so R has the singular values
+// and right singular vectors of B, and the Jacobi sweeps run on cols x cols.
+void householder_r(std::vector<cd>& B, int rows, int cols, std::vector<cd>& R) {
+  R.assign((size_t)cols * cols, cd(0.0, 0.0));
+  for (int k = 0; k < cols; ++k) {
+    cd* bk = &B[(size_t)k * rows];
+    double tail = 0.0;
+    for (int i = k + 1; i < rows; ++i) tail += std::norm(bk[i]);
+    const cd x0 = bk[k];
+    const double ax0 = std::abs(x0), xn = std::sqrt(ax0 * ax0 + tail);
+    cd alpha(0.0, 0.0);
+    if (xn > 0.0) {
+      // v = x - alpha e_k with alpha = -e^{i arg x0} |x|: |v|^2 = (|x0| + |x|)^2 + tail, no cancellation
+      const cd ph = ax0 > 0.0 ? x0 / ax0 : cd(1.0, 0.0);
+      alpha = -ph * xn;
+      bk[k] = x0 - alpha;
+      const double vn2 = (ax0 + xn) * (ax0 + xn) + tail;
+      for (int j = k + 1; j < cols; ++j) {
+        cd* bj = &B[(size_t)j * rows];
+        cd w(0.0, 0.0);
+        for (int i = k; i < rows; ++i) w += std::conj(bk[i]) * bj[i];
+        const cd f = 2.0 * w / vn2;
+        for (int i = k; i < rows; ++i) bj[i] -= f * bk[i];
+      }
+    }
+    R[(size_t)k * cols + k] = alpha;
+    for (int j = k + 1; j < cols; ++j) R[(size_t)j * cols + k] = B[(size_t)j * rows + k];
   }
 }
 
@@ -471,13 +503,14 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
       ++row;
     }
   }
-  std::vector<cd> Vj;
-  one_sided_jacobi(B, rows, na, Vj);
+  std::vector<cd> R, Vj;
+  householder_r(B, rows, na, R);
+  one_sided_jacobi(R, na, na, Vj);
   int jmin = 0;
   double smin = 1e300, smax = 0.0;
   for (int j = 0; j < na; ++j) {
     double s = 0.0;
-    for (int i = 0; i < rows; ++i) s += std::norm(B[(size_t)j * rows + i]);
+    for (int i = 0; i < na; ++i) s += std::norm(R[(size_t)j * na + i]);
     s = std::sqrt(s);
     if (s < smin) { smin = s; jmin = j; }
     smax = std::max(smax, s);

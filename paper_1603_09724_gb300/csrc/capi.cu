@@ -1165,13 +1165,17 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
       OMM_TRY(build_spp(h));
       h->spp_poles.assign(P, SppPole());
       std::vector<std::vector<cd>> gh(P);
-      const int nth = std::max(1, std::min<int>(P, (int)std::thread::hardware_concurrency()));
+      // one thread per pole; host cores beyond the poles factor each pole's elimination tree
+      // with up to 4 threads (the factor is the same bitwise)
+      const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+      const int nth = std::max(1, std::min<int>(P, hw));
+      const int tpp = std::max(1, std::min(4, hw / nth));
       std::vector<std::thread> th;
       for (int t = 0; t < nth; ++t)
         th.emplace_back([&, t]() {
           for (int j = t; j < P; j += nth)
             spp_setup_pole(h->spp, h->kin, h->Vh.data(), h->shift, cd(z[2 * j], z[2 * j + 1]), h->prm.pivot_floor,
-                           h->spp_poles[j], gh[j]);
+                           h->spp_poles[j], gh[j], tpp);
         });
       for (auto& t : th) t.join();
       h->nq = (int)h->spp.offsets.size() / 3;

@@ -10,8 +10,11 @@
 //   (pivots below pivot_floor * row size are raised and counted).
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <mutex>
 #include <set>
+#include <thread>
 
 #include "spp.h"
 
@@ -252,7 +255,13 @@ inline void caxpy_sub(int len, cd a, const cd* x, cd* y) {
 // panel's rank-kPanel update one row at a time, with the panel's rows of U in cache.
 // Rows and terms with a zero multiplier are skipped.  A pivot below pivot_floor times the
 // largest entry of its updated row is raised to that size (static pivoting) and counted.
-void partial_lu(cd* F, int nf, int ns, double pivot_floor, SppPole& out) {
+// Pivot statistics of the static pivoting, accumulated per thread and merged
+struct PivotStats {
+  double pmin = 1e300, pmax = 0.0;
+  int nperturbed = 0;
+};
+
+void partial_lu(cd* F, int nf, int ns, double pivot_floor, PivotStats& out) {
   constexpr int kPanel = 32;
   const cd zero(0.0, 0.0);
   for (int kb = 0; kb < ns; kb += kPanel) {
@@ -271,8 +280,8 @@ void partial_lu(cd* F, int nf, int ns, double pivot_floor, SppPole& out) {
         rk[k] = piv;
         ++out.nperturbed;
       }
-      out.pivot_min = std::min(out.pivot_min, std::abs(piv));
-      out.pivot_max = std::max(out.pivot_max, std::abs(piv));
+      out.pmin = std::min(out.pmin, std::abs(piv));
+      out.pmax = std::max(out.pmax, std::abs(piv));
       const cd ip = 1.0 / piv;
       for (int i = k + 1; i < nf; ++i) {
         cd* ri = F + (size_t)i * nf;
@@ -468,7 +477,7 @@ void green_symbol(int dim, int m, double kin, double lmean, double shift, cd z, 
 }
 
 void spp_setup_pole(const SppStructure& st, double kin, const double* V, double shift, cd z, double pivot_floor,
-                    SppPole& out, std::vector<cd>& ghat) {
+                    SppPole& out, std::vector<cd>& ghat, int threads) {
   const int dim = st.dim, m = st.m, n = st.n;
   double lmean = 0.0;
   for (int i = 0; i < n; ++i) lmean += V[i];
@@ -535,16 +544,18 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
   // ---- multifrontal LU
   out.factor.assign((size_t)st.factor_size, cd(0.0, 0.0));
   out.leafval.assign((size_t)st.leaf_size, cd(0.0, 0.0));
-  out.pivot_min = 1e300;
-  out.pivot_max = 0.0;
-  out.nperturbed = 0;
   const int nn = (int)st.nodes.size();
   std::vector<std::vector<cd>> upd(nn);
   std::vector<std::vector<int>> children(nn);
   for (int i = 0; i < nn; ++i)
     if (st.nodes[i].parent >= 0) children[st.nodes[i].parent].push_back(i);
-  std::vector<int> loc(n, -1);
-  for (int s = 0; s < nn; ++s) {
+  // One supernode: assemble its front from P's couplings and its children's update
+  // matrices (in the fixed order of `children`), eliminate, store W_f / W_b (and the
+  // banded leaf data), keep the update matrix for the parent.  It reads only its own
+  // front, its children's update matrices and st, and writes only its own slices of
+  // out.factor / out.leafval and upd[s]: nodes whose subtrees are disjoint can run on
+  // different threads, each with its own loc (unknown -> front position) and stats.
+  auto factor_node = [&](int s, std::vector<int>& loc, PivotStats& ps) {
     const SppNode& nd = st.nodes[s];
     const int ns = nd.ns, nb = nd.nb, nf = ns + nb;
     for (int i = 0; i < ns; ++i) loc[nd.off + i] = i;
@@ -576,7 +587,7 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
     const bool leaf = children[s].empty() && !st.leaf_nodes.empty();   // banded leaf data (2D) is kept
     std::vector<cd> F0;
     if (leaf) F0 = F;   // original couplings of the leaf (no children: F holds only P's entries)
-    partial_lu(F.data(), nf, ns, pivot_floor, out);
+    partial_lu(F.data(), nf, ns, pivot_floor, ps);
     // W_f = [L_SS^-1 ; L_BS L_SS^-1], W_b = [U_SS^-1 , -U_SS^-1 U_SB]: with these, each
     // supernode's forward and backward step is one dense product on the device.  All four
     // are formed row by row from contiguous rows (zero coefficients skipped).
@@ -652,6 +663,53 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
       for (int j = 0; j < nb; ++j) upd[s][(size_t)i * nb + j] = F[(size_t)(ns + i) * nf + ns + j];
     for (int i = 0; i < ns; ++i) loc[nd.off + i] = -1;
     for (int j = 0; j < nb; ++j) loc[st.bnd[nd.boff + j]] = -1;
+  };
+  // Tree schedule: a node is ready once its children are factorised; with one thread this
+  // is the index (post-) order.  Every node's arithmetic is the same on any thread, so the
+  // factor is bitwise independent of the thread count.
+  const int T = std::max(1, std::min(threads, 16));
+  std::vector<PivotStats> stats(T);
+  if (T == 1) {
+    std::vector<int> loc(n, -1);
+    for (int s = 0; s < nn; ++s) factor_node(s, loc, stats[0]);
+  } else {
+    std::vector<int> pending(nn), ready;
+    for (int s = 0; s < nn; ++s) {
+      pending[s] = (int)children[s].size();
+      if (pending[s] == 0) ready.push_back(s);
+    }
+    std::mutex mu;
+    std::condition_variable cv;
+    int done = 0;
+    auto worker = [&](int t) {
+      std::vector<int> loc(n, -1);
+      std::unique_lock<std::mutex> lk(mu);
+      for (;;) {
+        cv.wait(lk, [&] { return !ready.empty() || done == nn; });
+        if (ready.empty()) return;                 // every node is factorised
+        const int s = ready.back();                // depth first: the most recently readied node
+        ready.pop_back();
+        lk.unlock();
+        factor_node(s, loc, stats[t]);
+        lk.lock();
+        ++done;
+        const int par = st.nodes[s].parent;
+        if (par >= 0 && --pending[par] == 0) ready.push_back(par);
+        cv.notify_all();
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(worker, t);
+    worker(0);
+    for (auto& th : pool) th.join();
+  }
+  out.pivot_min = 1e300;
+  out.pivot_max = 0.0;
+  out.nperturbed = 0;
+  for (const PivotStats& ps : stats) {
+    out.pivot_min = std::min(out.pivot_min, ps.pmin);
+    out.pivot_max = std::max(out.pivot_max, ps.pmax);
+    out.nperturbed += ps.nperturbed;
   }
 }
 

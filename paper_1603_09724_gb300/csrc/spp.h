@@ -71,8 +71,10 @@ SppStructure spp_build_structure(int dim, int m, int r);
 // Per pole: q by the SVD of G(a, a^c), P assembly, multifrontal LU with static pivoting.
 // kin: (2 pi^2 / L^2); V: n reals; shift: sigma; z: pole.  ghat_out (n) receives
 // 1/(T(k) + l - sigma - z) / n (the Green symbol with the inverse-DFT scale folded in).
+// threads: workers for the supernodes of this pole's elimination tree (1 = sequential);
+// the factor is bitwise the same for any value.
 void spp_setup_pole(const SppStructure& st, double kin, const double* V, double shift, cd z, double pivot_floor,
-                    SppPole& out, std::vector<cd>& ghat_out);
+                    SppPole& out, std::vector<cd>& ghat_out, int threads = 1);
 
 // Green symbol only (for the kinetic inner preconditioner).
 void green_symbol(int dim, int m, double kin, double lmean, double shift, cd z, std::vector<cd>& ghat_out);

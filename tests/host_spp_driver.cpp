@@ -4,12 +4,14 @@
 // update rows summed by the ancestor in CSR order; 2D leaves also through their banded
 // L/U and halo couplings) and prints x = P^-1 b.
 //
+// argv[1] (optional): threads for the elimination tree (default 1)
 // stdin:  dim m L shift z_re z_im, then n values of V, then n pairs (re, im) of b
 // stdout: "dense" then n pairs of x (every node through W), and for 2D "banded" then n
 //         pairs of x (leaves through the banded data)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "spp.h"
@@ -106,7 +108,8 @@ static std::vector<cd> replay(const SppStructure& st, const SppPole& pp, const s
   return x;
 }
 
-int main() {
+int main(int argc, char** argv) {
+  const int threads = argc > 1 ? std::atoi(argv[1]) : 1;
   int dim, m;
   double L, shift, zr, zi;
   if (scanf("%d %d %lf %lf %lf %lf", &dim, &m, &L, &shift, &zr, &zi) != 6) return 2;
@@ -123,7 +126,7 @@ int main() {
   }
   SppPole pp;
   std::vector<cd> gh;
-  spp_setup_pole(st, 2.0 * M_PI * M_PI / (L * L), V.data(), shift, cd(zr, zi), 1e-12, pp, gh);
+  spp_setup_pole(st, 2.0 * M_PI * M_PI / (L * L), V.data(), shift, cd(zr, zi), 1e-12, pp, gh, threads);
   for (int mode = 0; mode < (st.leaf_nodes.empty() ? 1 : 2); ++mode) {
     printf("%s\n", mode ? "banded" : "dense");
     for (const cd& v : replay(st, pp, b, mode == 1)) printf("%.17g %.17g\n", v.real(), v.imag());

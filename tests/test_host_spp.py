@@ -4,7 +4,8 @@ driver that replays the device triangular-solve algorithm on the host, against t
 SuperLU solve of the same P (oracle.sparsify).  2D and 3D grids; in 2D both the dense-W and
 the banded-leaf paths.  q is unique up to a unit phase, which scales P and so P^-1 b by one
 global phase: the comparison removes it.  Built with AddressSanitizer where the compiler
-supports it, so an out-of-bounds access in the host setup fails the test."""
+supports it, so an out-of-bounds access in the host setup fails the test.  The elimination
+tree factorised on 2 and 4 threads gives bitwise the same solve as on one."""
 import os
 import shutil
 import subprocess
@@ -34,12 +35,15 @@ def driver(tmp_path_factory):
     pytest.fail("host_spp_driver does not compile")
 
 
-def run_driver(exe, dim, m, L, V, shift, z, b):
+def run_driver(exe, dim, m, L, V, shift, z, b, threads=1, raw=False):
     f = lambda v: repr(float(v))
     lines = [f"{dim} {m} {f(L)} {f(shift)} {f(z.real)} {f(z.imag)}", " ".join(f(v) for v in V),
              " ".join(f"{f(v.real)} {f(v.imag)}" for v in b)]
-    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=600)
+    r = subprocess.run([exe, str(threads)], input="\n".join(lines) + "\n", capture_output=True, text=True,
+                       timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
+    if raw:
+        return r.stdout
     out, cur = {}, None
     for ln in r.stdout.splitlines():
         if ln in ("dense", "banded"):
@@ -70,3 +74,15 @@ def test_host_factor_solves_the_oracle_P(driver, dim, m, L):
         err, scale = phase_free_err(x, ref)
         assert err < 1e-9, (mode, err)
         assert abs(scale - 1.0) < 1e-9, (mode, scale)
+
+
+@pytest.mark.parametrize("dim,m,L", [(2, 32, 10.0), (3, 8, 20.0)])
+def test_threaded_tree_factorisation_is_bitwise_identical(driver, dim, m, L):
+    shape = (m,) * dim
+    V = wells_2d(m, L, seed=5) if dim == 2 else lattice_wells_3d(m, L, cells=2)
+    shift = ham.default_shift(shape, L, V)
+    z = complex(-0.3 * shift, 1.1)
+    n = m ** dim
+    b = np.random.default_rng(7).standard_normal(n) + 1j * np.random.default_rng(8).standard_normal(n)
+    outs = [run_driver(driver, dim, m, L, V, shift, z, b, threads=t, raw=True) for t in (1, 2, 4)]
+    assert outs[0] == outs[1] == outs[2]

@@ -158,7 +158,9 @@ omm_status omm_poles_circle(double center, double radius, int P, double* z, doub
  * (eq. P), its nested-dissection multifrontal LU (host, FP64) and uploads the factors.
  * With real_orbitals the conjugate pairs are folded first (see omm_params).  A projector
  * built by omm_build_projector no longer applies after new poles and is dropped.
- * Errors: OMM_EINVAL, OMM_ENOMEM, OMM_ECUDA. */
+ * Errors: OMM_EINVAL (P out of range, a non-finite z or w, an unpaired pole with
+ * real_orbitals: the previous poles stay), OMM_ENOMEM, OMM_ECUDA (the handle then has no
+ * poles until a later call succeeds: calls that need them return OMM_ESTATE). */
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w);
 
 /* Copy the current orbitals in (X: device, n x N, handle precision) or out. */
@@ -247,7 +249,8 @@ omm_status omm_drop_projector(omm_t h);
  * fused FFT / multiply / inverse-FFT pass per application), ahead of a projector or the pole
  * expansion, and omm_solve starts the CG from the orbitals as given (no filter step).
  * omm_filter keeps filtering with the pole expansion or the projector.  Poles are not needed.
- * Errors: OMM_EINVAL (t, c or tau out of range), OMM_ENOMEM, OMM_ECUDA. */
+ * Errors: OMM_EINVAL (t, c or tau out of range; a gTPA preconditioner already set stays),
+ * OMM_ENOMEM, OMM_ECUDA (no gTPA preconditioner is then set). */
 omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau);
 
 /* Stop using the gTPA preconditioner (back to the projector or the pole expansion). */

@@ -1132,6 +1132,8 @@ static bool fold_conjugate_pairs(int P, const double* z, const double* w, std::v
 
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
   if (!h || !z || !w || P < 1 || P > PMAX) return OMM_EINVAL;
+  for (int j = 0; j < 2 * P; ++j)
+    if (!std::isfinite(z[j]) || !std::isfinite(w[j])) return OMM_EINVAL;
   std::vector<double> zf, wf;
   if (h->prm.real_orbitals) {
     if (!fold_conjugate_pairs(P, z, w, zf, wf)) {
@@ -1142,6 +1144,9 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
     z = zf.data();
     w = wf.data();
   }
+  // from here on the handle's pole data changes: it counts as set again only once every
+  // buffer below holds the new poles (a failure leaves OMM_ESTATE, not a mix of old and new)
+  h->poles_set = false;
   h->real_combine = h->prm.real_orbitals != 0;
   h->use_proj = false;   // a projector built from other poles no longer applies
   h->P = P;
@@ -1577,6 +1582,7 @@ omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau) {
   }
   const size_t n = h->n;
   const int m = h->m;
+  h->use_gtpa = false;   // set again once the new table is on the device
   std::vector<cd> tab(2 * n);
   auto sk = [m](int i) { return i < m / 2 ? i : i - m; };
   for (size_t i = 0; i < n; ++i) {

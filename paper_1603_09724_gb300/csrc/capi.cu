@@ -113,6 +113,10 @@ struct omm_ctx {
   size_t gw_dbg_bytes = 0;
   void* m64 = nullptr;          // residual-check N x N matrices and two norms
   int Pfac = 0;                 // poles the factor buffers are sized for
+  // allocation groups: set only once every buffer of the group exists and is initialised,
+  // so that a failed allocation is retried in full by the next call (a byte or pole count
+  // is likewise reset before its buffer is replaced)
+  bool fp64_ready = false, ghat_ready = false, proj_ready = false;
 
   // poles
   int P = 0;
@@ -366,6 +370,7 @@ omm_status greenq(omm_ctx* h, const void* B, void* Out, int ncols, int nq, int c
 
 omm_status ensure_dbg_work(omm_ctx* h, size_t need) {
   if (h->gw_dbg_bytes >= need) return OMM_OK;
+  h->gw_dbg_bytes = 0;
   OMM_TRY(h->dalloc(&h->gw_dbg, need));
   h->gw_dbg_bytes = need;
   return OMM_OK;
@@ -374,6 +379,7 @@ omm_status ensure_dbg_work(omm_ctx* h, size_t need) {
 omm_status ensure_fft_tmp(omm_ctx* h, size_t ncols, bool dbl) {
   const size_t need = ncols * h->n * (dbl ? 16 : 8);
   if (h->fft_tmp_bytes >= need) return OMM_OK;
+  h->fft_tmp_bytes = 0;
   OMM_TRY(h->dalloc(&h->fft_tmp, need));   // the old buffer stays owned until destroy
   h->fft_tmp_bytes = need;
   return OMM_OK;
@@ -414,6 +420,7 @@ omm_status upload_vec(omm_ctx* h, T_** dst, const std::vector<T_>& v) {
 
 omm_status ensure_gmres_work(omm_ctx* h, int P) {
   if (h->Palloc >= P) return OMM_OK;
+  h->Palloc = 0;
   const size_t S = (size_t)P * h->N;
   const size_t vb = S * h->n * h->csz;
   const int m = h->prm.gmres_m;
@@ -658,12 +665,15 @@ omm_status gram_any(omm_ctx* h, const void* A, int na, const void* B, int nb, do
   if (!h->dbl && h->prm.gram_tensor && gram_tc_supported(h->n)) {
     const size_t need = gram_tc_work_bytes(na, nb, h->n);
     if (need > h->tc_work_bytes) {
+      h->tc_work_bytes = 0;
       OMM_TRY(h->dalloc(&h->tc_work, need));
       h->tc_work_bytes = need;
     }
     if (!h->tc_err) {
-      OMM_TRY(h->dalloc_t(&h->tc_err, sizeof(int)));
-      OMM_TRY(cuda_status(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st), "memset"));
+      int* flag = nullptr;
+      OMM_TRY(h->dalloc_t(&flag, sizeof(int)));
+      OMM_TRY(cuda_status(cudaMemsetAsync(flag, 0, sizeof(int), h->st), "memset"));
+      h->tc_err = flag;
     }
     return cuda_status(launch_gram_tc(A, na, B, nb, h->n, C, ldc, h->tc_work, h->tc_err, h->st), "gram_tc");
   }
@@ -780,11 +790,12 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
 omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
   const int N = h->N;
   const size_t cnt = (size_t)N * h->n;
-  if (!h->X64) {
+  if (!h->fp64_ready) {
     OMM_TRY(h->dalloc(&h->X64, cnt * 16 * 3));   // [X | HX | R] in FP64
     OMM_TRY(h->dalloc_t(&h->gram64, (size_t)N * 2 * N * sizeof(double2)));
     OMM_TRY(h->dalloc(&h->gram64_work, gram_work_bytes(N, 2 * N, h->n)));
     OMM_TRY(h->dalloc_t(&h->tmp_shift, sizeof(double2) * 2));
+    h->fp64_ready = true;
   }
   void* X64 = h->X64;
   void* HX64 = (char*)h->X64 + cnt * 16;
@@ -1191,6 +1202,7 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
       }
       const long long fs = h->spp.factor_size;
       if (h->Pfac < P) {
+        h->Pfac = 0;
         OMM_TRY(h->dalloc(&h->factor, (size_t)P * fs * h->csz));
         OMM_TRY(h->dalloc(&h->leafvals, (size_t)P * h->spp.leaf_size * h->csz));
         OMM_TRY(h->dalloc(&h->ubuf, (size_t)h->spp.urows * P * h->N * h->csz));
@@ -1214,9 +1226,10 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
       h->nq = 1;
       q_all.assign(P, cd(1.0, 0.0));
     }
-    if (!h->ghat) {
+    if (!h->ghat_ready) {
       OMM_TRY(h->dalloc(&h->ghat, (size_t)PMAX * n * h->csz));
       OMM_TRY(h->dalloc(&h->qd, (size_t)PMAX * 27 * h->csz));
+      h->ghat_ready = true;
     }
     OMM_TRY(upload_complex(h, h->ghat, ghat_all, h->dbl));
     OMM_TRY(upload_complex(h, h->qd, q_all, h->dbl));
@@ -1464,7 +1477,7 @@ omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st)
   const int N = h->N;
   if (ncols != N && ncols != 2 * N) return OMM_EINVAL;
   const size_t cnt = (size_t)N * h->n;
-  if (!h->Uproj) {
+  if (!h->proj_ready) {
     OMM_TRY(h->dalloc(&h->Uproj, cnt * h->csz));
     OMM_TRY(h->dalloc(&h->projM, (size_t)N * N * h->csz));
     OMM_TRY(h->dalloc(&h->projZero, (size_t)N * N * h->csz));
@@ -1476,6 +1489,7 @@ omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st)
     OMM_TRY(h->dalloc(&h->projZero64, (size_t)N * N * 16));
     OMM_TRY(h->dalloc(&h->projWork64, gram_work_bytes(2 * N, 2 * N, h->n)));
     OMM_TRY(cuda_status(cudaMemsetAsync(h->projZero64, 0, (size_t)N * N * 16, h->st), "memset"));
+    h->proj_ready = true;
   }
   h->use_proj = false;
   void* Y64 = h->projY64;                      // Y1, then Y2 at + cnt (2N contiguous columns)
@@ -1600,8 +1614,10 @@ omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau) {
     tab[n + i] = cd(-g / (double)n, 0.0);
   }
   if (!h->gtpa_one) {
-    OMM_TRY(h->dalloc(&h->gtpa_one, h->csz));
-    OMM_TRY(upload_complex(h, h->gtpa_one, std::vector<cd>(1, cd(1.0, 0.0)), h->dbl));
+    void* one = nullptr;
+    OMM_TRY(h->dalloc(&one, h->csz));
+    OMM_TRY(upload_complex(h, one, std::vector<cd>(1, cd(1.0, 0.0)), h->dbl));
+    h->gtpa_one = one;
   }
   if (!h->gtpa_tab) OMM_TRY(h->dalloc(&h->gtpa_tab, 2 * n * h->csz));
   OMM_TRY(upload_complex(h, h->gtpa_tab, tab, h->dbl));

@@ -8,7 +8,8 @@ Admission is by device-memory footprint: a request waits until its handle fits t
 budget, evicting idle resident handles (least recently used) when needed.  Up to
 `slots` solves run at the same time, each on its own CUDA stream and host thread (the
 library's calls release the GIL), so their kernels overlap on the device; a new request
-is admitted as soon as a slot and memory free up.  Latency = completion - arrival.
+is admitted as soon as a slot and memory free up.  Latency = completion - arrival.  A
+request that fails (a library error) comes back as a Result with `error` set.
 
 All device work is the library's (libomm.so); this module only schedules it.
 """
@@ -45,11 +46,12 @@ class Request:
 class Result:
     rid: int
     key: str
-    X: np.ndarray
+    X: Optional[np.ndarray]
     stats: dict
     latency_s: float
     queue_s: float
     warm: bool
+    error: Optional[str] = None       # set (and X None) when the request failed
 
 
 class _Resident:
@@ -139,14 +141,21 @@ class OmmServer:
             out.append(self.results.get(timeout=max(1.0, timeout - (time.perf_counter() - t0))))
         return out
 
-    def close(self):
+    def close(self, timeout: float = 600.0):
+        """Stop admitting, wait (up to timeout) for the solves in flight, then free every
+        resident handle."""
         with self.cv:
             self.stop = True
             self.cv.notify_all()
         self.sched.join(timeout=10)
-        for r in list(self.resident.values()):
-            r.solver.close()
-        self.resident.clear()
+        t_end = time.perf_counter() + timeout
+        with self.cv:
+            while self.active > 0 and time.perf_counter() < t_end:
+                self.cv.wait(timeout=0.05)
+            for r in list(self.resident.values()):
+                if not r.busy:
+                    r.solver.close()
+            self.resident.clear()
 
     def resident_bytes(self) -> int:
         return sum(r.bytes for r in self.resident.values())
@@ -216,19 +225,25 @@ class OmmServer:
 
     def _run(self, req: Request):
         omm, dev = self.omm, self.dev
-        dev.set_device(self.device)
         t_start = time.perf_counter()
         res = self.resident.get(req.key)
         warm = res is not None and res.X is not None
         try:
+            dev.set_device(self.device)
             if res is None:
                 stream = dev.new_stream()
-                with dev.stream_ctx(stream):
-                    prm = omm.default_params(**self.params)
-                    s = omm.Solver(req.dim, req.m, req.L, req.V, req.N, shift=req.sigma, params=prm,
-                                   stream=dev.stream_handle(stream))
-                    z, w = omm.poles_fermi(req.lam1, req.lamN, req.lamN1, req.P)
-                    s.set_poles(z, w)
+                s = None
+                try:
+                    with dev.stream_ctx(stream):
+                        prm = omm.default_params(**self.params)
+                        s = omm.Solver(req.dim, req.m, req.L, req.V, req.N, shift=req.sigma, params=prm,
+                                       stream=dev.stream_handle(stream))
+                        z, w = omm.poles_fermi(req.lam1, req.lamN, req.lamN1, req.P)
+                        s.set_poles(z, w)
+                except BaseException:
+                    if s is not None:      # created but not set up: never becomes resident
+                        s.close()
+                    raise
                 res = _Resident(s, s.device_bytes(), stream)
                 res.busy = True
                 with self.cv:
@@ -252,6 +267,10 @@ class OmmServer:
                 Xh = dev.download(X)
             done = time.perf_counter()
             self.results.put(Result(req.rid, req.key, Xh, st, done - req.arrival, t_start - req.arrival, warm))
+        except Exception as e:   # the caller gets a failed result instead of waiting for one
+            done = time.perf_counter()
+            self.results.put(Result(req.rid, req.key, None, {}, done - req.arrival, t_start - req.arrival, warm,
+                                    error=repr(e)))
         finally:
             with self.cv:
                 self.creating.discard(req.key)
@@ -265,7 +284,9 @@ class OmmServer:
 
 
 def latency_summary(results: list[Result], wall_s: float) -> dict:
-    lat = np.array([r.latency_s for r in results])
-    return {"requests": len(results), "solves_per_s": len(results) / wall_s,
+    """Throughput and latency of the completed solves; failed requests are counted apart."""
+    ok = [r for r in results if r.error is None]
+    lat = np.array([r.latency_s for r in ok]) if ok else np.zeros(1)
+    return {"requests": len(results), "failed": len(results) - len(ok), "solves_per_s": len(ok) / wall_s,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "warm_fraction": float(np.mean([r.warm for r in results]))}
+            "warm_fraction": float(np.mean([r.warm for r in ok])) if ok else 0.0}

@@ -174,13 +174,16 @@ omm_status omm_filter(omm_t h);
 
 /* k steps of Algorithm 1 from the current X (restarting the CG: the first step uses the
  * steepest preconditioned direction).  st may be NULL.  Returns OMM_OK, or OMM_ESHIFT if
- * the quartic was not bounded below; OMM_ESTATE if neither poles nor gTPA are set. */
+ * the quartic was not bounded below; OMM_ESTATE if neither poles nor gTPA are set;
+ * OMM_ENOTCONV (st filled, fewer than k steps) if the energy, the line-search step or the
+ * Polak-Ribiere beta became non-finite (numerical breakdown; the message says so). */
 omm_status omm_iterate(omm_t h, int k, omm_stats* st);
 
 /* Whole solve: filter, CG until the energy criterion or maxit, then refilter rounds,
  * then the FP64 energy and residual of the result (with gTPA set: one CG round from the
  * given orbitals, no filter).  Returns OMM_ENOTCONV (with st filled) if maxit was reached
- * in the last round; OMM_ESTATE if neither poles nor gTPA are set. */
+ * in the last round or the CG broke down on a non-finite energy, step or beta (then no
+ * further rounds run); OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_solve(omm_t h, omm_stats* st);
 
 /* E_omm of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams). */

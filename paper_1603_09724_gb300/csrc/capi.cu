@@ -117,6 +117,7 @@ struct omm_ctx {
   // so that a failed allocation is retried in full by the next call (a byte or pole count
   // is likewise reset before its buffer is replaced)
   bool fp64_ready = false, ghat_ready = false, proj_ready = false;
+  bool breakdown = false;       // the last CG run met a non-finite energy / step / beta
 
   // poles
   int P = 0;
@@ -726,6 +727,7 @@ omm_status start_cg(omm_ctx* h) {
 }
 
 omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* conv) {
+  h->breakdown = false;
   OMM_TRY(start_cg(h));
   const size_t cnt = (size_t)h->N * h->n;
   *conv = false;
@@ -766,6 +768,14 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
     if (h->sc_h->bad) {
       *done_iters = it + 1;
       return OMM_ESHIFT;
+    }
+    if (!std::isfinite(h->sc_h->E1) || !std::isfinite(h->sc_h->t) || !std::isfinite(h->sc_h->beta)) {
+      // numerical breakdown (a non-finite Gram, quartic or step): stop, not converged,
+      // instead of iterating on NaN to maxit
+      h->breakdown = true;
+      omm_internal_set_message("non-finite energy, line-search step or beta in the CG");
+      ++it;
+      break;
     }
     if (h->sc_h->converged) {
       *conv = true;
@@ -1270,6 +1280,7 @@ omm_status omm_iterate(omm_t h, int k, omm_stats* st) {
     st->iters = done;
     st->converged = conv;
   }
+  if (s == OMM_OK && h->breakdown) s = OMM_ENOTCONV;
   return s;
 }
 
@@ -1292,6 +1303,7 @@ omm_status omm_solve(omm_t h, omm_stats* st) {
     int done = 0;
     OMM_TRY(cg_steps(h, h->prm.maxit, &loc, &done, &conv));
     total += done;
+    if (h->breakdown) break;
   }
   loc.iters = total;
   loc.converged = conv;

@@ -101,3 +101,46 @@ def test_create_rejects_non_finite_inputs_before_touching_the_device():
                dict(pivot_floor=np.nan), dict(pivot_floor=-1e-12), dict(tol=np.inf)):
         assert create(V, shift, omm.default_params(**kw)) == omm.OMM_EINVAL, kw
     assert not h.value
+
+
+def test_failing_allocator_hook_leaks_nothing():
+    """Fault injection through omm_set_allocator: the k-th of omm_create's device
+    allocations fails (k = 1..18, all of which come before its first CUDA runtime call):
+    the call returns OMM_ENOMEM, leaves no handle, makes no further allocation and has
+    released every block it got."""
+    import ctypes as C
+    import numpy as np
+    import paper_1603_09724_gb300 as omm
+    ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+    FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+    live, state = {}, {"calls": 0, "fail_at": 0, "bad_free": 0}
+
+    def alloc(size, ctx):
+        state["calls"] += 1
+        if state["calls"] == state["fail_at"]:
+            return None
+        buf = C.create_string_buffer(int(size))
+        live[C.addressof(buf)] = buf
+        return C.addressof(buf)
+
+    def release(p, ctx):
+        if live.pop(p, None) is None:
+            state["bad_free"] += 1
+
+    a_cb, f_cb = ALLOC(alloc), FREE(release)
+    m, L = 16, 10.0
+    V = np.zeros(m * m)
+    g = omm.make_grid(2, m, L)
+    shift = 2 * (2 * np.pi ** 2 / L ** 2 * 2 * (m // 2) ** 2)
+    h = C.c_void_p()
+    assert omm.lib.omm_set_allocator(a_cb, f_cb, None) == omm.OMM_OK
+    try:
+        for k in range(1, 19):
+            state.update(calls=0, fail_at=k)
+            rc = omm.lib.omm_create(C.byref(g), V.ctypes.data_as(C.POINTER(C.c_double)), 4, shift, None, None,
+                                    C.byref(h))
+            assert rc == omm.OMM_ENOMEM and not h.value, k
+            assert state["calls"] == k and not live and state["bad_free"] == 0, k
+    finally:
+        omm.lib.omm_set_allocator(None, None, None)
+    assert omm.lib.omm_set_allocator(a_cb, None, None) == omm.OMM_EINVAL   # both hooks or neither

@@ -27,7 +27,7 @@ def _rank(rank, world, port, out):
 def test_two_replicas_take_the_slowest_rank():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that already runs threads
     out = mgr.dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):

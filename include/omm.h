@@ -121,7 +121,8 @@ const char* omm_strerror(omm_status s);
 const char* omm_last_error_message(void);
 
 /* Defaults: FP64, sparsifying inner preconditioner, GMRES(15) x 5 cycles, rtol 1e-5
- * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter. */
+ * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter.
+ * Errors: OMM_EINVAL (p NULL). */
 omm_status omm_default_params(omm_params* p);
 
 /* Diagonal shift (Sec. 1): sigma = T_max + max(max V, 0) + 1e-3 (T_max + max V - min V),
@@ -163,7 +164,8 @@ omm_status omm_poles_circle(double center, double radius, int P, double* z, doub
  * poles until a later call succeeds: calls that need them return OMM_ESTATE). */
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w);
 
-/* Copy the current orbitals in (X: device, n x N, handle precision) or out. */
+/* Copy the current orbitals in (X: device, n x N, handle precision) or out.
+ * Errors: OMM_EINVAL (NULL handle or X), OMM_ECUDA. */
 omm_status omm_set_orbitals(omm_t h, const void* X);
 omm_status omm_get_orbitals(omm_t h, void* X);
 
@@ -186,25 +188,32 @@ omm_status omm_iterate(omm_t h, int k, omm_stats* st);
  * further rounds run); OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_solve(omm_t h, omm_stats* st);
 
-/* E_omm of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams). */
+/* E_omm of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams).
+ * Errors: OMM_EINVAL (NULL handle or E), OMM_ENOMEM (first call allocates the FP64
+ * work space), OMM_ECUDA. */
 omm_status omm_energy(omm_t h, double* E);
 
 /* ---- building blocks on caller buffers (the steps of one iteration) ------------ */
 
 /* Y = (H - sigma - s) X for ncols columns: X, Y device, n x ncols, handle precision;
- * s = s_re + i s_im (pass s = -sigma for the unshifted -Delta/2 + V). */
+ * s = s_re + i s_im (pass s = -sigma for the unshifted -Delta/2 + V).
+ * Errors: OMM_EINVAL (NULL pointers, ncols < 0), OMM_ENOMEM, OMM_ECUDA. */
 omm_status omm_apply_h(omm_t h, const void* X, void* Y, int ncols, double s_re, double s_im);
 
 /* C = A^* B (na x nb, complex128, row-major, device, ldc = nb): A, B device blocks of
- * na and nb columns in the handle precision. */
+ * na and nb columns in the handle precision.
+ * Errors: OMM_EINVAL (NULL pointers, na or nb < 1), OMM_ENOMEM, OMM_ECUDA, OMM_ETIMEOUT (a
+ * bounded wait of the tensor-core Gram gave up; the flag stays set for the handle). */
 omm_status omm_gram(omm_t h, const void* A, int na, const void* B, int nb, void* C);
 
 /* Grad = 2 HX - X (X^*HX) - HX (X^*X) with H = H - sigma (Sec. 2.1): X device block of
- * N columns; HX and Grad device blocks (HX computed internally; may be NULL). */
+ * N columns; HX and Grad device blocks (HX computed internally; may be NULL).
+ * Errors: OMM_EINVAL (NULL handle, X or Grad), OMM_ENOMEM, OMM_ECUDA, OMM_ETIMEOUT. */
 omm_status omm_gradient(omm_t h, const void* X, void* HX, void* Grad);
 
 /* Quartic coefficients c[5] of E_omm(X + tD) and the exact line-search step *t
- * (host outputs); X, D device blocks of N columns. */
+ * (host outputs); X, D device blocks of N columns.
+ * Errors: OMM_EINVAL (NULL handle, X or D), OMM_ECUDA, OMM_ETIMEOUT. */
 omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double* t);
 
 /* Sparsifying preconditioner of pole j on ncols columns: U = P_j^-1 Q_j (G_j B)
@@ -215,7 +224,9 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
 /* Pole-expansion preconditioner on N columns: Y = sum_j w_j Y_j with Y_j the GMRES
  * solution of (H - sigma - z_j) Y_j = R started from R (Sec. 3.1 eqs. direct, lst); with a
  * projector built (omm_build_projector), Y = U U^* R; with gTPA set (omm_set_gtpa), Y = P_t R.
- * R, Y device blocks of N columns.  st may be NULL (fills the gmres_* fields). */
+ * R, Y device blocks of N columns.  st may be NULL (fills the gmres_* fields).
+ * Errors: OMM_EINVAL (NULL pointers), OMM_ESTATE (neither poles nor gTPA set), OMM_ENOMEM,
+ * OMM_ECUDA, OMM_ETIMEOUT. */
 omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
 
 /* Precomputed preconditioner (Sec. 3.3, Algorithm 2): Y = sum_j w_j Y_j with
@@ -235,7 +246,8 @@ omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
 omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st);
 
 /* Return to the pole-expansion preconditioner (frees nothing; U is kept until the next
- * omm_build_projector or omm_destroy). */
+ * omm_build_projector or omm_destroy).
+ * Errors: OMM_EINVAL (NULL handle). */
 omm_status omm_drop_projector(omm_t h);
 
 /* Fourier-diagonal comparison preconditioner of Sec. 2.2 (eqs. Lap, TPA, gTPA), the
@@ -256,12 +268,15 @@ omm_status omm_drop_projector(omm_t h);
  * OMM_ENOMEM, OMM_ECUDA (no gTPA preconditioner is then set). */
 omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau);
 
-/* Stop using the gTPA preconditioner (back to the projector or the pole expansion). */
+/* Stop using the gTPA preconditioner (back to the projector or the pole expansion).
+ * Errors: OMM_EINVAL (NULL handle). */
 omm_status omm_drop_gtpa(omm_t h);
 
 /* Statistics of the sparsifying factor of pole j (host outputs, any may be NULL):
  * number of supernodes, factor entries (L + U), smallest |pivot| / largest |pivot|,
- * number of perturbed pivots. */
+ * number of perturbed pivots.
+ * Errors: OMM_EINVAL (NULL handle, pole out of range), OMM_ESTATE (no poles, or the inner
+ * preconditioner is not the sparsifying one). */
 omm_status omm_factor_info(omm_t h, int pole, int* nsuper, long long* nnz, double* pivot_ratio, int* nperturbed);
 
 /* C = A^* B like omm_gram, but without a handle and without allocating any device
@@ -284,10 +299,11 @@ omm_status omm_gram_noalloc(int precision, const void* A, int na, const void* B,
                             void* stream);
 
 /* Device allocator hook used by subsequent omm_create calls (NULL, NULL restores
- * cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or NULL. */
+ * cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or NULL.
+ * Errors: OMM_EINVAL (exactly one of alloc and release is NULL). */
 omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx);
 
-/* Bytes of device memory the handle holds. */
+/* Bytes of device memory the handle holds.  Errors: OMM_EINVAL (NULL handle or bytes). */
 omm_status omm_device_bytes(omm_t h, size_t* bytes);
 
 /* ---- instrumentation (no counterpart in the paper; used to report roofline figures) --
@@ -298,7 +314,8 @@ omm_status omm_device_bytes(omm_t h, size_t* bytes);
  * calls, kernels launched and algorithmic bytes moved; with profiling enabled it also
  * brackets each call with CUDA events on the handle's stream and sums the elapsed
  * milliseconds.  omm_profile_enable(h, 1) resets the counters; omm_profile_read
- * synchronises the stream.  omm_profile_class_name returns NULL for an unknown class. */
+ * synchronises the stream.  omm_profile_class_name returns NULL for an unknown class.
+ * Errors: OMM_EINVAL (NULL handle, class out of range). */
 omm_status omm_profile_enable(omm_t h, int on);
 omm_status omm_profile_read(omm_t h, int cls, long long* calls, long long* kernels, double* ms, double* bytes);
 const char* omm_profile_class_name(int cls);

@@ -115,9 +115,10 @@ typedef struct {
   int gmres_iters_total;   /* sum of GMRES steps over all CG iterations (max per call) */
 } omm_stats;
 
-/* Human-readable text for a status code (static storage). */
+/* Human-readable text for a status code (static storage; no counterpart in the paper). */
 const char* omm_strerror(omm_status s);
-/* Text of the last CUDA failure recorded by this thread (static per-thread storage). */
+/* Text of the last CUDA failure or refusal reason recorded by this thread (static per-thread
+ * storage; no counterpart in the paper). */
 const char* omm_last_error_message(void);
 
 /* Defaults: FP64, sparsifying inner preconditioner, GMRES(15) x 5 cycles, rtol 1e-5
@@ -130,7 +131,8 @@ omm_status omm_default_params(omm_params* p);
  * V: host, n doubles.  Errors: OMM_EINVAL. */
 omm_status omm_default_shift(const omm_grid* g, const double* V, double* shift);
 
-/* Create a handle.  V: host, n doubles, copied.  N: number of states (1 <= N < n).
+/* Create a handle for H = -Delta/2 + V - sigma on the grid (Sec. 4 eq. ex1mat, shifted as in
+ * Sec. 1).  V: host, n doubles, copied.  N: number of states (1 <= N < n).
  * shift: sigma; must exceed T_max + max V (else OMM_ESHIFT).  p: NULL for defaults.
  * stream: a cudaStream_t (NULL = legacy default stream).  Allocates the device work
  * space of the CG on the current device (the GMRES work space of the poles is allocated
@@ -164,7 +166,8 @@ omm_status omm_poles_circle(double center, double radius, int P, double* z, doub
  * poles until a later call succeeds: calls that need them return OMM_ESTATE). */
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w);
 
-/* Copy the current orbitals in (X: device, n x N, handle precision) or out.
+/* Copy the current orbitals X of eq. omm (the start of Algorithm 1) in (X: device, n x N,
+ * handle precision) or out.
  * Errors: OMM_EINVAL (NULL handle or X), OMM_ECUDA. */
 omm_status omm_set_orbitals(omm_t h, const void* X);
 omm_status omm_get_orbitals(omm_t h, void* X);
@@ -181,26 +184,29 @@ omm_status omm_filter(omm_t h);
  * Polak-Ribiere beta became non-finite (numerical breakdown; the message says so). */
 omm_status omm_iterate(omm_t h, int k, omm_stats* st);
 
-/* Whole solve: filter, CG until the energy criterion or maxit, then refilter rounds,
+/* Whole solve (Algorithm 1 with the filtered start of Sec. 4): filter, CG until the energy
+ * criterion or maxit, then refilter rounds,
  * then the FP64 energy and residual of the result (with gTPA set: one CG round from the
  * given orbitals, no filter).  Returns OMM_ENOTCONV (with st filled) if maxit was reached
  * in the last round or the CG broke down on a non-finite energy, step or beta (then no
  * further rounds run); OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_solve(omm_t h, omm_stats* st);
 
-/* E_omm of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams).
+/* E_omm (eq. omm) of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams).
  * Errors: OMM_EINVAL (NULL handle or E), OMM_ENOMEM (first call allocates the FP64
  * work space), OMM_ECUDA. */
 omm_status omm_energy(omm_t h, double* E);
 
 /* ---- building blocks on caller buffers (the steps of one iteration) ------------ */
 
-/* Y = (H - sigma - s) X for ncols columns: X, Y device, n x ncols, handle precision;
+/* The pseudospectral H-apply (Sec. 4 eq. ex1mat), shifted as in eq. lst:
+ * Y = (H - sigma - s) X for ncols columns: X, Y device, n x ncols, handle precision;
  * s = s_re + i s_im (pass s = -sigma for the unshifted -Delta/2 + V).
  * Errors: OMM_EINVAL (NULL pointers, ncols < 0), OMM_ENOMEM, OMM_ECUDA. */
 omm_status omm_apply_h(omm_t h, const void* X, void* Y, int ncols, double s_re, double s_im);
 
-/* C = A^* B (na x nb, complex128, row-major, device, ldc = nb): A, B device blocks of
+/* The Gram blocks of eq. omm and Sec. 2.1 (X^*X, X^*HX, ...):
+ * C = A^* B (na x nb, complex128, row-major, device, ldc = nb): A, B device blocks of
  * na and nb columns in the handle precision.
  * Errors: OMM_EINVAL (NULL pointers, na or nb < 1), OMM_ENOMEM, OMM_ECUDA, OMM_ETIMEOUT (a
  * bounded wait of the tensor-core Gram gave up; the flag stays set for the handle). */
@@ -211,7 +217,8 @@ omm_status omm_gram(omm_t h, const void* A, int na, const void* B, int nb, void*
  * Errors: OMM_EINVAL (NULL handle, X or Grad), OMM_ENOMEM, OMM_ECUDA, OMM_ETIMEOUT. */
 omm_status omm_gradient(omm_t h, const void* X, void* HX, void* Grad);
 
-/* Quartic coefficients c[5] of E_omm(X + tD) and the exact line-search step *t
+/* The exact line search of Algorithm 1 on eq. omm: quartic coefficients c[5] of
+ * E_omm(X + tD) and its minimising step *t
  * (host outputs); X, D device blocks of N columns.
  * Errors: OMM_EINVAL (NULL handle, X or D), OMM_ECUDA, OMM_ETIMEOUT. */
 omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double* t);
@@ -245,7 +252,8 @@ omm_status omm_pole_solve(omm_t h, const void* R, void* Y, omm_stats* st);
  * rank deficient (a Cholesky pivot <= 0). */
 omm_status omm_build_projector(omm_t h, const void* B, int ncols, omm_stats* st);
 
-/* Return to the pole-expansion preconditioner (frees nothing; U is kept until the next
+/* Return to the pole-expansion preconditioner (Sec. 3.1) from U U^* (Sec. 3.3; frees
+ * nothing; U is kept until the next
  * omm_build_projector or omm_destroy).
  * Errors: OMM_EINVAL (NULL handle). */
 omm_status omm_drop_projector(omm_t h);
@@ -268,11 +276,12 @@ omm_status omm_drop_projector(omm_t h);
  * OMM_ENOMEM, OMM_ECUDA (no gTPA preconditioner is then set). */
 omm_status omm_set_gtpa(omm_t h, int t, const double* c, double tau);
 
-/* Stop using the gTPA preconditioner (back to the projector or the pole expansion).
+/* Stop using the gTPA preconditioner of Sec. 2.2 (back to the projector or the pole
+ * expansion).
  * Errors: OMM_EINVAL (NULL handle). */
 omm_status omm_drop_gtpa(omm_t h);
 
-/* Statistics of the sparsifying factor of pole j (host outputs, any may be NULL):
+/* Statistics of the sparsifying factor of pole j (Sec. 3.2; host outputs, any may be NULL):
  * number of supernodes, factor entries (L + U), smallest |pivot| / largest |pivot|,
  * number of perturbed pivots.
  * Errors: OMM_EINVAL (NULL handle, pole out of range), OMM_ESTATE (no poles, or the inner
@@ -298,12 +307,13 @@ omm_status omm_factor_info(omm_t h, int pole, int* nsuper, long long* nnz, doubl
 omm_status omm_gram_noalloc(int precision, const void* A, int na, const void* B, int nb, size_t n, void* C,
                             void* stream);
 
-/* Device allocator hook used by subsequent omm_create calls (NULL, NULL restores
+/* Device allocator hook (no counterpart in the paper) used by subsequent omm_create calls
+ * (NULL, NULL restores
  * cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or NULL.
  * Errors: OMM_EINVAL (exactly one of alloc and release is NULL). */
 omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx);
 
-/* Bytes of device memory the handle holds.  Errors: OMM_EINVAL (NULL handle or bytes). */
+/* Bytes of device memory the handle holds (no counterpart in the paper).  Errors: OMM_EINVAL (NULL handle or bytes). */
 omm_status omm_device_bytes(omm_t h, size_t* bytes);
 
 /* ---- instrumentation (no counterpart in the paper; used to report roofline figures) --

@@ -308,12 +308,13 @@ omm_status omm_gram_noalloc(int precision, const void* A, int na, const void* B,
                             void* stream);
 
 /* Device allocator hook (no counterpart in the paper) used by subsequent omm_create calls
- * (NULL, NULL restores
- * cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or NULL.
+ * (NULL, NULL restores cudaMalloc/cudaFree).  alloc(bytes, ctx) returns device memory or
+ * NULL.
  * Errors: OMM_EINVAL (exactly one of alloc and release is NULL). */
 omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx);
 
-/* Bytes of device memory the handle holds (no counterpart in the paper).  Errors: OMM_EINVAL (NULL handle or bytes). */
+/* Bytes of device memory the handle holds (no counterpart in the paper).
+ * Errors: OMM_EINVAL (NULL handle or bytes). */
 omm_status omm_device_bytes(omm_t h, size_t* bytes);
 
 /* ---- instrumentation (no counterpart in the paper; used to report roofline figures) --

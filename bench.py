@@ -48,9 +48,14 @@ def args_parse():
     ap.add_argument("--iters", type=int, default=0, help="fixed CG iterations (0: energy criterion)")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the untimed FP64-form comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", type=int, default=1, help="per-kernel CUDA-event timing in the timed region")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="1: per-class CUDA events inside the timed region (perturbs it); 0: counters only there")
+    ap.add_argument("--no-profile-pass", dest="profile_pass", action="store_false",
+                    help="skip the untimed per-class profile solve after the timed region")
     ap.add_argument("--refilter", type=int, default=0, help="extra filter + CG rounds after convergence")
     ap.add_argument("--rtol", type=float, default=1e-5, help="GMRES relative tolerance (paper: 1e-5)")
+    ap.add_argument("--refilter-rtol", type=float, default=0.0,
+                    help="GMRES tolerance of the refilter rounds (0: --rtol)")
     ap.add_argument("--N", type=int, default=0, help="override N (reduced case for profiler captures only)")
     ap.add_argument("--P", type=int, default=0, help="override P (reduced case for profiler captures only)")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
@@ -129,7 +134,8 @@ def inner_choice(wl, inner="auto"):
     return inner
 
 
-def workload_config(wl, spectra, iters, precision="mixed", refilter=0, rtol=1e-5, orbitals="real", inner="auto"):
+def workload_config(wl, spectra, iters, precision="mixed", refilter=0, rtol=1e-5, orbitals="real", inner="auto",
+                    refilter_rtol=0.0):
     return {"workload": f"{wl.name}: {wl.dim}D {wl.m}^{wl.dim} periodic grid (n={wl.n}), N={wl.N} states, "
                         f"P={wl.P} conformal poles, {wl.potential} potential, {precision}",
             "orbitals": ("real X, conjugate pole pairs folded (P/2 GMRES solves per application)"
@@ -139,36 +145,57 @@ def workload_config(wl, spectra, iters, precision="mixed", refilter=0, rtol=1e-5
                                      if inner_choice(wl, inner) == "spp" else
                                      "kinetic (T + <V> - sigma - z)^-1 (the sparsifying factor is not built above 16^3)"),
             "gmres": f"restart 15, <=5 cycles, rtol {rtol:g}", "cg_iters": iters if iters else "energy criterion",
-            "refilter": refilter,
+            "refilter": refilter, **({"refilter_rtol": refilter_rtol} if refilter and refilter_rtol else {}),
             "l2": "inputs/working set larger than L2 (GMRES basis ~GBs)", "parallelism": "replicas",
             "spectral_interval": "stored exact [lam_1, lam_N], lam_{N+1} (workloads/spectra.json)"}
 
 
 # ------------------------------------------------------------------------------ CPU oracle timing
-def oracle_sample(wl, spectra, budget_s=12.0):
-    """Time the FP64 oracle's pole solves (the dominant work) on a bounded sample and
-    extrapolate to solves/s: one solve = (1 filter + CG iterations) preconditioner
-    applications, each P x N GMRES solves."""
-    import numpy as np
+def oracle_setup(wl, spectra):
+    """The FP64 oracle's pole-expansion preconditioner for the workload: all P poles, each
+    with its own sparsifying factor (SuperLU) or Green symbol; built once, outside any
+    timed sample."""
     from oracle import poles as opoles
     from oracle.precond import PolePreconditioner
     V = wl.potential_values()
     z, w = opoles.poles_conformal(spectra["lam1"], spectra["lamN"], spectra["lamN1"], wl.P)
-    X0 = wl.initial_block()
-    cols = 2
-    pc = PolePreconditioner(wl.shape, wl.L, V, spectra["sigma"], z[:1], w[:1], mode="gmres",
-                            inner="spp" if inner_choice(wl) == "spp" else "lap")
-    t0 = time.perf_counter()
-    c0 = time.process_time()
-    reps = 0
+    return PolePreconditioner(wl.shape, wl.L, V, spectra["sigma"], z, w, mode="gmres",
+                              inner="spp" if inner_choice(wl) == "spp" else "lap")
+
+
+def oracle_unit(pc, X0, rep, cols):
+    """One sample unit of the oracle's dominant work: the whole pole expansion (every pole's
+    GMRES + sparsifying solve) applied to `cols` columns of the starting block.  Returns
+    (wall seconds, CPU seconds, mean GMRES steps per system of the unit)."""
+    import numpy as np
+    nblk = X0.shape[0] // cols
+    k = rep % nblk
+    n0 = len(pc.stats)
+    t0, c0 = time.perf_counter(), time.process_time()
+    pc(X0[k * cols:(k + 1) * cols])
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    its = [float(np.mean(st["iters"])) for st in pc.stats[n0:] if "iters" in st]
+    return wall, cpu, (float(np.mean(its)) if its else float("nan"))
+
+
+def oracle_sample(wl, spectra, budget_s=12.0, pc=None):
+    """Time the oracle's pole expansion (all P poles, 2 columns per unit) for about
+    budget_s seconds; returns (seconds per unit, columns per unit, host cores used, mean
+    GMRES steps per system, units)."""
+    import numpy as np
+    pc = pc or oracle_setup(wl, spectra)
+    X0 = wl.initial_block(np.complex128, real=True)
+    cols, walls, cpus, its = 2, [], [], []
     while True:
-        pc(X0[reps % (wl.N // cols) * cols:(reps % (wl.N // cols) + 1) * cols])
-        reps += 1
-        if time.perf_counter() - t0 > budget_s:
+        wall, cpu, it = oracle_unit(pc, X0, len(walls), cols)
+        walls.append(wall)
+        cpus.append(cpu)
+        its.append(it)
+        if sum(walls) > budget_s:
             break
-    wall = time.perf_counter() - t0
-    cores = (time.process_time() - c0) / wall   # host threads the oracle actually kept busy
-    return wall / reps, cols, round(max(cores, 1.0), 1)
+    t = sum(walls) / len(walls)
+    cores = round(max(sum(cpus) / sum(walls), 1.0), 1)   # host threads the oracle kept busy
+    return t, cols, cores, float(np.nanmean(its)), len(walls)
 
 
 def threads_used():
@@ -179,13 +206,18 @@ def threads_used():
         return 1
 
 
-def cpu_baseline_record(wl, spectra, applications):
-    t, cols, cores = oracle_sample(wl, spectra)
-    per_solve = t * (wl.P * wl.N / cols) * applications
+def cpu_baseline_record(wl, spectra, applications, gpu_gmres_mean=None):
+    t, cols, cores, its, units = oracle_sample(wl, spectra)
+    per_solve = t * (wl.N / cols) * applications
+    gpu = f"; the GPU solve's largest GMRES step count per application averages {gpu_gmres_mean:.1f}" \
+        if gpu_gmres_mean else ""
     return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": (f"oracle GMRES+sparsifying pole solve, 1 pole x {cols} columns ({t:.2f} s), scaled by "
-                       f"P*N/{cols} systems x {applications} preconditioner applications per solve; pocketfft and "
-                       f"SuperLU, BLAS pool {threads_used()} threads; cores = CPU time / wall time of the sample")}
+            "sample": (f"{units} units of the oracle's pole expansion, each all {wl.P} poles (GMRES + "
+                       f"{'sparsifying' if inner_choice(wl) == 'spp' else 'kinetic'} preconditioner, no conjugate "
+                       f"folding) on {cols} starting columns ({t:.2f} s per unit); scaled by N/{cols} column pairs x "
+                       f"{applications} applications per solve; the oracle's GMRES took {its:.1f} steps per system "
+                       f"on average{gpu}; pocketfft and SuperLU, BLAS pool {threads_used()} threads; "
+                       f"cores = CPU time / wall time of the sample")}
 
 
 def cpu_baseline_gtpa(wl, spectra, t, iters, real=True, sample_iters=8):
@@ -209,31 +241,42 @@ def cpu_baseline_gtpa(wl, spectra, t, iters, real=True, sample_iters=8):
 
 
 def run_reference(a):
+    """The oracle as it stands, on the host cores: each step is one bounded sample unit of
+    the workload (the whole pole expansion, all P poles, on two starting columns), timed;
+    the line's value scales the median unit to one whole solve."""
+    import numpy as np
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl, spectra = load_workload(a.workload)
-    # CG iterations of one solve of this workload (measured on the GPU arm, FP64 form):
-    # the sample is extrapolated to 1 filter + that many preconditioner applications
+    # CG iterations of one solve of this workload (measured on the GPU arm): the sample
+    # is scaled to 1 filter + that many preconditioner applications
     cg_iters = {"smooth2d-128": 20, "wells2d-32": 13, "lattice3d-48": 21}.get(wl.name, 12)
     applications = 1 + (a.iters or cg_iters)
-    t0 = time.perf_counter()
-    vals, used = [], []
-    for s in range(a.warmup + a.steps):
-        t, cols, cores = oracle_sample(wl, spectra, budget_s=4.0)
-        if s >= a.warmup:
-            vals.append(1.0 / (t * (wl.P * wl.N / cols) * applications))
-            used.append(cores)
-    wall = time.perf_counter() - t0
-    v = statistics.median(vals)
+    pc = oracle_setup(wl, spectra)                  # untimed: SuperLU factors of every pole
+    X0 = wl.initial_block(np.complex128, real=True)
+    cols = 2
+    walls, cpus, its = [], [], []
+    for s_ in range(a.warmup + a.steps):
+        wall, cpu, it = oracle_unit(pc, X0, s_, cols)
+        if s_ >= a.warmup:
+            walls.append(wall)
+            cpus.append(cpu)
+            its.append(it)
+    t = statistics.median(walls)
+    v = 1.0 / (t * (wl.N / cols) * applications)
+    cores = round(max(sum(cpus) / sum(walls), 1.0), 1)
     rec = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": a.gpus,
-           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(wl, spectra, a.iters, "fp64 oracle", orbitals=a.orbitals, inner=a.inner),
-           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": max(used), "kind": "oracle",
-                            "sample": f"each step: one oracle pole solve (1 pole x 2 columns, ~4 s), extrapolated "
-                                      f"to P*N systems x {applications} applications per solve (the oracle solves every pole, "
-                                      f"no conjugate folding); wall {wall:.1f} s"},
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * sum(walls) / len(walls),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(workload_config(wl, spectra, a.iters, "fp64 oracle", orbitals="complex", inner=a.inner),
+                          orbitals="complex X: the oracle solves every pole (no conjugate folding)"),
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": f"each step: the oracle's whole pole expansion (all {wl.P} poles, GMRES + "
+                                      f"sparsifying preconditioner) on {cols} starting columns, "
+                                      f"{statistics.median(walls):.2f} s median; value = 1 / (that x N/{cols} x "
+                                      f"{applications} applications per solve); oracle GMRES {np.nanmean(its):.1f} "
+                                      f"steps per system on average"},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(rec))
 
@@ -280,7 +323,8 @@ def run_ours(a):
     real = a.orbitals == "real"
     inner = omm.OMM_INNER_SPARSIFY if inner_choice(wl, a.inner) == "spp" else omm.OMM_INNER_KINETIC
     prm = omm.default_params(precision=prec, maxit=maxit, tol=tol, refilter=a.refilter, gmres_rtol=a.rtol,
-                             real_orbitals=int(real), inner=inner, gram_tensor=a.gram_tensor)
+                             real_orbitals=int(real), inner=inner, gram_tensor=a.gram_tensor,
+                             refilter_rtol=a.refilter_rtol, gap=spectra["lamN1"] - spectra["lamN"])
     s = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
     t_setup = time.perf_counter()
     if a.precond == "gtpa":
@@ -320,8 +364,9 @@ def run_ours(a):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    if a.profile:
-        s.profile(True)
+    # the timed region runs with the kernel counters only (no per-class CUDA events); the
+    # per-class profile comes from a separate untimed solve below
+    s.profile(True if a.profile else "count")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -337,9 +382,8 @@ def run_ours(a):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    prof = s.profile_read() if a.profile else None
-    if a.profile:
-        s.profile(False)
+    counts = s.profile_read()
+    s.profile(False)
     clk = clocks.stop()
     lat_ms = sorted(x.elapsed_time(y) for x, y in lat)
     ms_max, value = aggregate_ranks(ms, a.steps, world, "cuda")
@@ -368,15 +412,32 @@ def run_ours(a):
         e2e_ms = f0.elapsed_time(f1)
     nbytes = X0h.numel() * X0h.element_size()
 
+    # per-class profile: one more solve (untimed) with CUDA events around every kernel class
+    prof = None
+    if a.profile_pass and not a.profile:
+        s.profile(True)
+        st_p = step()
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        prof_ms = sum(v["ms"] for v in prof.values())
+        s.profile(False)
+    elif a.profile:
+        prof, prof_ms = counts, ms
+
     if rank != 0:
         return
     peaks = measured_peaks()
+    apps = st["filters"] + st["iters"]
     rec = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64" if mixed else "c128", "data": "synthetic",
+           "gpu_launches": int(sum(v["kernels"] for v in counts.values())),
            "config": dict(workload_config(wl, spectra, a.iters, "mixed" if mixed else "fp64", a.refilter, a.rtol,
-                                          a.orbitals, a.inner),
+                                          a.orbitals, a.inner, a.refilter_rtol),
                           preconditioner=precond_text(a, spectra),
+                          timing=("CUDA events on the handle's stream around the whole timed region; kernel "
+                                  "counters on, per-class events off" if not a.profile else
+                                  "per-class CUDA events on inside the timed region (--profile 1)"),
                           **({"l2": "working set (six n x N blocks, ~100 MB) fits in L2: a 512 MB write flushes "
                                     "L2 before every timed solve"} if a.precond == "gtpa" else {})),
            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
@@ -384,66 +445,99 @@ def run_ours(a):
                      "energy_fp64": st["energy_fp64"], "resid_fp64": st["resid_fp64"],
                      "E_rel_err_vs_exact": abs(st["energy_fp64"] - spectra["E_ref"]) / abs(spectra["E_ref"]),
                      "gmres_iters_max": st["gmres_iters_max"], "gmres_iters_total": st["gmres_iters_total"],
+                     "grad_norm": st["grad_norm"], "resid_orth": st["resid_orth"], "angle_bound": st["angle_bound"],
                      "setup_s_all_poles": t_setup},
            "clocks": clk,
            "e2e": ({"value": world * a.steps / (e2e_ms / 1000.0), "unit": "solves/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes} if e2e_ms else None)}
     if prof:
         dom = max(prof, key=lambda k: prof[k]["ms"])
-        rec["gpu_launches"] = int(sum(v["kernels"] for v in prof.values()))
         kern = {}
         for k, v in prof.items():
             if v["calls"]:
                 kern[k] = {"calls": v["calls"], "kernels": v["kernels"], "ms": round(v["ms"], 3),
-                           "share": round(v["ms"] / max(ms, 1e-9), 4),
-                           "GB_s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1) if v["bytes"] else None}
-        rec["kernels"] = kern
-        rec["roofline"] = roofline_record(prof, dom, wl.N, wl.n, peaks, clk.get("sm_mhz"), a.gram_tensor)
+                           "share": round(v["ms"] / max(prof_ms, 1e-9), 4),
+                           "GB_s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1) if v["bytes"] else None,
+                           **({"impl_GB_s": round(v["impl_bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                              if v.get("impl_bytes") and abs(v["impl_bytes"] - v["bytes"]) > 1e-6 * v["bytes"]
+                              else {})}
+        rec["kernels"] = {"pass": ("one untimed solve with per-class CUDA events after the timed region"
+                                   if not a.profile else "the timed region"), "classes": kern}
+        rec["roofline"] = roofline_record(prof, dom, wl, peaks, clk.get("sm_mhz"), a.gram_tensor, apps)
         ha = prof["happly"]
         rec["happly_GB_s"] = ha["bytes"] / max(ha["ms"], 1e-9) / 1e6
     if not a.no_fp64_check and world == 1:
-        rec["accuracy_vs_fp64"] = fp64_compare(a, wl, spectra, s, omm, torch, V, z, w)
+        acc = fp64_compare(a, wl, spectra, s, omm, torch, V, z, w)
+        rec["accuracy_vs_fp64"] = acc
+        if "sin_angle" in acc:
+            rec["accuracy_gates"] = {"E_rel_diff_vs_fp64_form": acc["E_rel_diff"], "E_gate": 1e-8,
+                                     "sin_angle_vs_fp64_form": acc["sin_angle"], "sin_gate": 1e-6,
+                                     "pass": bool(acc["E_rel_diff"] <= 1e-8 and acc["sin_angle"] <= 1e-6)}
     if not a.no_cpu_baseline:
         rec["cpu_baseline"] = (cpu_baseline_gtpa(wl, spectra, a.gtpa_t, st["iters"], real) if a.precond == "gtpa"
-                               else cpu_baseline_record(wl, spectra, st["filters"] + st["iters"]))
+                               else cpu_baseline_record(wl, spectra, apps, st["gmres_iters_total"] / max(apps, 1)))
     print(json.dumps(rec))
+
+
+# DRAM bytes one call of a kernel class moved in an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum summed over the class's kernels for one call, scaled to the bench
+# workload's systems), keyed by class; a class is absent until captured for its current
+# kernels.
+TRAFFIC_PER_CALL = {}
 
 
 SMS, FP32_LANES_PER_SM = 152, 128          # GB300: 152 SMs x 4 partitions x 32 FP32 lanes
 TF32_PER_BF16 = 1.1 / 2.25                 # nominal dense tensor-core rates, TF32 / BF16
 
 
-def roofline_record(prof, dom, N, n, peaks, sm_mhz, gram_tensor):
-    """Roofline of the dominant kernel class `dom` from the library's CUDA-event profile.
+def roofline_record(prof, dom, wl, peaks, sm_mhz, gram_tensor, apps):
+    """Roofline of the dominant kernel class `dom` from the untimed per-class profile.
 
-    HBM-bound classes: algorithmic bytes / event time against the measured copy bandwidth.
-    The Gram class (it dominates only when the preconditioner is cheap, e.g. gTPA) is
-    compute-bound: 48 n N^2 algorithmic real flops per fused Gram [X D]^* [X D HX HD] (its
-    6 N^2 distinct complex entries, 8 flops per complex multiply-add), every call counted as
-    one such Gram; against FP32 FMA on the CUDA cores (SMs x 128 lanes x 2 flops x the median
-    SM clock of the timed region), or, on tcgen05, the measured bf16 rate x the nominal
-    TF32 / BF16 ratio."""
+    HBM-bound classes: the class's algorithmic bytes (the library's count: H-apply 2v plus V,
+    Green 2v plus the symbol tables, CGS2 (2(k+1)+3) vectors, triangular solves 4 per
+    unknown and active system plus the factor) / its CUDA-event time, against the measured
+    copy bandwidth.  The Gram class (it dominates only when the preconditioner is cheap,
+    e.g. gTPA) is compute-bound: 48 n N^2 algorithmic real flops per fused Gram [X D]^*
+    [X D HX HD] (its 6 N^2 distinct complex entries, 8 flops per complex multiply-add),
+    every call counted as one such Gram; against FP32 FMA on the CUDA cores (SMs x 128 lanes
+    x 2 flops x the median SM clock of the timed region), or, on tcgen05, the measured bf16
+    rate x the nominal TF32 / BF16 ratio."""
     d = prof[dom]
     ms = max(d["ms"], 1e-9)
+    N, n = wl.N, wl.n
     if dom == "gram":
         flops = d["calls"] * 48.0 * n * N * N
         ach = flops / ms / 1e9                                  # TFLOP/s
         if gram_tensor:
             peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
-            bound, how = "tensor", "measured bf16 GEMM rate x nominal TF32/BF16 ratio"
+            bound, how = "tensor", "measured bf16 GEMM rate x nominal TF32/BF16 ratio (of measured)"
         else:
             mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
             peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
             bound, how = "alu", f"FP32 FMA on the CUDA cores at {mhz:.0f} MHz"
         return {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None,
-                "note": f"achieved = 48 n N^2 flops per Gram call / CUDA-event time over the timed region; peak = {how}"}
+                "note": f"achieved = 48 n N^2 flops per Gram call / CUDA-event time of the profile solve; peak = {how}"}
     hbm = peaks.get("hbm_gbs", 6800.0)
     ach = d["bytes"] / ms / 1e6
+    per_call = d["bytes"] / max(d["calls"], 1)
+    formula = {
+        "trsv_levels": "per application: 4 x n_sep x 8 B per active system (rhs in, y out, y in, x out) + the "
+                       "separator blocks W_f, W_b of every pole once",
+        "trsv_leaf": "per application: 4 x n_leaf x 8 B per active system + the leaf factor values of every pole once",
+        "happly": "2 x n x 8 B per column (X in, Y out) + V",
+        "greenq": "2 x n x 8 B per column + the Green symbol of each pole",
+        "orth": "(2(k+1) + 3) x n x 8 B per active system at Arnoldi step k",
+    }.get(dom, "the library's algorithmic byte count")
+    tr = TRAFFIC_PER_CALL.get(dom)
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None,
-            "note": "achieved = algorithmic bytes / CUDA-event time summed over the class's launches in the timed "
-                    "region; peak = measured copy bandwidth"}
+            "traffic": tr,
+            "algorithmic_bytes_per_call": per_call,
+            "impl_bytes_per_call": d.get("impl_bytes", d["bytes"]) / max(d["calls"], 1),
+            "note": (f"achieved = algorithmic bytes / CUDA-event time summed over the class's launches in one "
+                     f"untimed profile solve ({formula}); a call is one application of the class to all "
+                     f"systems (one GMRES step's triangular solves, H-apply, ...); peak = measured copy bandwidth "
+                     f"(of measured); traffic = DRAM bytes per call from ncu, or null")}
 
 
 def precond_text(a, spectra):
@@ -455,24 +549,36 @@ def precond_text(a, spectra):
             "eigenvectors (Sec. 4); CG from the unfiltered start")
 
 
-def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w):
-    """The same solve in the plain FP64 form (untimed): energy and subspace agreement."""
+def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w, timed=2):
+    """The same solve in the plain FP64 form (its own handle, poles set outside the timing):
+    energy and subspace agreement, and its solve time measured like the mixed line's
+    (CUDA events around `timed` solves after one untimed solve)."""
     import numpy as np
     try:
         Xm = s.get_orbitals().cpu().numpy().astype(np.complex128)
         real = a.orbitals == "real"
         prm = omm.default_params(precision=omm.OMM_FP64, maxit=a.iters if a.iters else 40,
                                  tol=0.0 if a.iters else 1e-13, refilter=a.refilter, gmres_rtol=a.rtol,
-                                 real_orbitals=int(real),
+                                 refilter_rtol=a.refilter_rtol, real_orbitals=int(real),
                                  inner=omm.OMM_INNER_SPARSIFY if inner_choice(wl, a.inner) == "spp"
                                  else omm.OMM_INNER_KINETIC)
         t0 = time.perf_counter()
         s64 = omm.Solver(wl.dim, wl.m, wl.L, V, wl.N, shift=spectra["sigma"], params=prm)
         s64.set_poles(z, w)
-        s64.set_orbitals(torch.from_numpy(wl.initial_block(np.complex128, real=real)).to("cuda"))
-        st = s64.solve()
+        X0 = torch.from_numpy(wl.initial_block(np.complex128, real=real)).to("cuda")
         torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
+        setup_s = time.perf_counter() - t0
+        s64.set_orbitals(X0)
+        st = s64.solve()                               # untimed first solve
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(timed):
+            s64.set_orbitals(X0)
+            st = s64.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1000.0 / timed
         X64 = s64.get_orbitals().cpu().numpy()
         Q1, _ = np.linalg.qr(Xm.T)
         Q2, _ = np.linalg.qr(X64.T)
@@ -482,7 +588,9 @@ def fp64_compare(a, wl, spectra, s, omm, torch, V, z, w):
         return {"E_rel_diff": abs(Em - st["energy_fp64"]) / abs(st["energy_fp64"]), "sin_angle": sin,
                 "fp64_form_iters": st["iters"], "fp64_form_E_rel_err_vs_exact":
                     abs(st["energy_fp64"] - spectra["E_ref"]) / abs(spectra["E_ref"]),
-                "fp64_form_solve_s": t64}
+                "fp64_form_solve_s": t64, "fp64_form_solves_per_s": 1.0 / t64, "fp64_form_setup_s": setup_s,
+                "fp64_form_timing": f"CUDA events around {timed} solves after one untimed solve; handle creation "
+                                    "and pole set-up outside"}
     except Exception as e:   # report, never hide
         return {"error": repr(e)}
 

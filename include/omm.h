@@ -101,6 +101,17 @@ typedef struct {
                            rule).  Several let the latency-bound top of the elimination
                            tree of one group overlap the other groups' work; use 1 when
                            many handles already run concurrently (serving).           */
+  int fixed_iters;      /* > 0: every CG round runs exactly this many iterations of
+                           Algorithm 1 (no energy test; a fixed launch schedule for
+                           timing and capture); 0: the energy criterion and maxit      */
+  double refilter_rtol; /* GMRES tolerance of the rounds after the first (the refilter
+                           and its CG iterations); 0: gmres_rtol.  The final subspace
+                           error follows the GMRES tolerance of the last round, so a
+                           tight value here buys the 1e-6 angle for a few applications */
+  double gap;           /* lambda_{N+1} - lambda_N of H, if known (> 0): omm_solve then
+                           reports the Davis-Kahan bound resid_orth / gap on the sine of
+                           the largest principal angle to the exact invariant subspace;
+                           0: not reported                                             */
 } omm_params;
 
 typedef struct {
@@ -113,6 +124,12 @@ typedef struct {
   double gmres_relres_max; /* largest GMRES residual estimate of the last pole solve   */
   int gmres_iters_max;     /* largest GMRES step count of the last pole solve          */
   int gmres_iters_total;   /* sum of GMRES steps over all CG iterations (max per call) */
+  double grad_norm;        /* ||Grad||_F of the last CG gradient (Sec. 2.1), FP64 sum   */
+  double resid_orth;       /* ||H Q - Q (Q^* H Q)||_F with Q = X R^-1, S = R^* R the
+                              Cholesky factor of X^* X: the residual of the orthonormal
+                              basis of span X, FP64 on the device (omm_solve)           */
+  double angle_bound;      /* resid_orth / omm_params.gap (sin theta theorem of Davis
+                              and Kahan); 0 when no gap is given                        */
 } omm_stats;
 
 /* Human-readable text for a status code (static storage; no counterpart in the paper). */
@@ -122,7 +139,8 @@ const char* omm_strerror(omm_status s);
 const char* omm_last_error_message(void);
 
 /* Defaults: FP64, sparsifying inner preconditioner, GMRES(15) x 5 cycles, rtol 1e-5
- * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter.
+ * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter,
+ * fixed_iters 0, refilter_rtol 0 (= gmres_rtol), gap 0 (no angle bound).
  * Errors: OMM_EINVAL (p NULL). */
 omm_status omm_default_params(omm_params* p);
 
@@ -185,9 +203,13 @@ omm_status omm_filter(omm_t h);
 omm_status omm_iterate(omm_t h, int k, omm_stats* st);
 
 /* Whole solve (Algorithm 1 with the filtered start of Sec. 4): filter, CG until the energy
- * criterion or maxit, then refilter rounds,
- * then the FP64 energy and residual of the result (with gTPA set: one CG round from the
- * given orbitals, no filter).  Returns OMM_ENOTCONV (with st filled) if maxit was reached
+ * criterion or maxit, then refilter rounds (GMRES at refilter_rtol),
+ * then the FP64 check of the result on the device (with gTPA set: one CG round from the
+ * given orbitals, no filter): X converted to complex128, FP64 H-apply and Grams
+ * S = X^* X, K = X^* (H - sigma) X; one CTA computes E_omm = tr K - 1/2 tr(S K) (eq. omm),
+ * the Cholesky factor S = R^* R, R^-1 and S^-1 K; FP64 block updates form the residuals
+ * HX - X S^-1 K and (HX - X S^-1 K) R^-1 (stats energy_fp64, resid_fp64, resid_orth,
+ * angle_bound).  Returns OMM_ENOTCONV (with st filled) if maxit was reached
  * in the last round or the CG broke down on a non-finite energy, step or beta (then no
  * further rounds run); OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_solve(omm_t h, omm_stats* st);
@@ -318,17 +340,25 @@ omm_status omm_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void
 omm_status omm_device_bytes(omm_t h, size_t* bytes);
 
 /* ---- instrumentation (no counterpart in the paper; used to report roofline figures) --
- * Kernel classes: 0 happly (H-apply), 1 greenq (Green symbol + Q stencil), 2 trsv
- * (sparsifying triangular solves, L and U), 3 orth (GMRES Gram-Schmidt), 4 gram,
- * 5 block_update (gradient), 6 vector (axpby, dots, GMRES vector updates),
- * 7 small (line search, Givens, counters).  For every class the handle always counts
+ * Kernel classes: 0 happly (H-apply), 1 greenq (Green symbol + Q stencil), 2 trsv_levels
+ * (sparsifying triangular solves above the leaves, L and U), 3 orth (GMRES Gram-Schmidt),
+ * 4 gram, 5 block_update (gradient), 6 vector (axpby, dots, GMRES vector updates),
+ * 7 small (line search, Givens, counters), 8 trsv_leaf (the leaves' L and U solves).  For every class the handle always counts
  * calls, kernels launched and algorithmic bytes moved; with profiling enabled it also
  * brackets each call with CUDA events on the handle's stream and sums the elapsed
- * milliseconds.  omm_profile_enable(h, 1) resets the counters; omm_profile_read
+ * milliseconds.  omm_profile_enable(h, 1) resets the counters and turns the events on;
+ * omm_profile_enable(h, 2) resets the counters with the events off (counting only, no
+ * timing overhead); omm_profile_enable(h, 0) turns the events off.  omm_profile_read
  * synchronises the stream.  omm_profile_class_name returns NULL for an unknown class.
- * Errors: OMM_EINVAL (NULL handle, class out of range). */
+ * Algorithmic bytes of the triangular solves (classes 2 and 8): 4 complex values per
+ * unknown and active system (right-hand side in, y out, y in, x out) plus every pole's
+ * factor once per application; omm_profile_read_impl returns the implementation's own
+ * byte model of the class (the update rows, assembled separator right-hand sides and
+ * boundary gathers included), equal to the algorithmic bytes for the other classes.
+ * Errors: OMM_EINVAL (NULL handle or output, class or mode out of range). */
 omm_status omm_profile_enable(omm_t h, int on);
 omm_status omm_profile_read(omm_t h, int cls, long long* calls, long long* kernels, double* ms, double* bytes);
+omm_status omm_profile_read_impl(omm_t h, int cls, double* impl_bytes);
 const char* omm_profile_class_name(int cls);
 
 #ifdef __cplusplus

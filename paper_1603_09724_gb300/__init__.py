@@ -34,13 +34,15 @@ class omm_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("inner", C.c_int), ("gmres_m", C.c_int), ("gmres_cycles", C.c_int),
                 ("gmres_rtol", C.c_double), ("gmres_fixed", C.c_int), ("stencil_radius", C.c_int),
                 ("pivot_floor", C.c_double), ("tol", C.c_double), ("maxit", C.c_int), ("refilter", C.c_int),
-                ("gram_tensor", C.c_int), ("real_orbitals", C.c_int), ("trsv_streams", C.c_int)]
+                ("gram_tensor", C.c_int), ("real_orbitals", C.c_int), ("trsv_streams", C.c_int),
+                ("fixed_iters", C.c_int), ("refilter_rtol", C.c_double), ("gap", C.c_double)]
 
 
 class omm_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("filters", C.c_int), ("converged", C.c_int), ("energy", C.c_double),
                 ("energy_fp64", C.c_double), ("resid_fp64", C.c_double), ("gmres_relres_max", C.c_double),
-                ("gmres_iters_max", C.c_int), ("gmres_iters_total", C.c_int)]
+                ("gmres_iters_max", C.c_int), ("gmres_iters_total", C.c_int), ("grad_norm", C.c_double),
+                ("resid_orth", C.c_double), ("angle_bound", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,6 +82,7 @@ _SIGS = {
     "omm_profile_enable": (C.c_int, [_vp, C.c_int]),
     "omm_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _dp, _dp]),
     "omm_profile_class_name": (C.c_char_p, [C.c_int]),
+    "omm_profile_read_impl": (C.c_int, [_vp, C.c_int, _dp]),
     "omm_gram_noalloc": (C.c_int, [C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_size_t, _vp, _vp]),
 }
 PROFILE_CLASSES = ("happly", "greenq", "trsv_levels", "orth", "gram", "block_update", "vector", "small", "trsv_leaf")
@@ -313,7 +316,10 @@ class Solver:
         return dict(nsuper=ns.value, nnz=nnz.value, pivot_ratio=pr.value, nperturbed=npt.value)
 
     def profile(self, on=True):
-        check(lib.omm_profile_enable(self.h, 1 if on else 0), "omm_profile_enable")
+        """True: reset the counters, CUDA-event timing on; 'count': reset, counting only
+        (no events); False: events off."""
+        mode = 2 if on == "count" else (1 if on else 0)
+        check(lib.omm_profile_enable(self.h, mode), "omm_profile_enable")
 
     def profile_read(self):
         out = {}
@@ -321,7 +327,9 @@ class Solver:
             calls, kern, ms, by = C.c_longlong(), C.c_longlong(), C.c_double(), C.c_double()
             check(lib.omm_profile_read(self.h, c, C.byref(calls), C.byref(kern), C.byref(ms), C.byref(by)),
                   "omm_profile_read")
-            out[name] = dict(calls=calls.value, kernels=kern.value, ms=ms.value, bytes=by.value)
+            ib = C.c_double()
+            check(lib.omm_profile_read_impl(self.h, c, C.byref(ib)), "omm_profile_read_impl")
+            out[name] = dict(calls=calls.value, kernels=kern.value, ms=ms.value, bytes=by.value, impl_bytes=ib.value)
         return out
 
     def device_bytes(self):

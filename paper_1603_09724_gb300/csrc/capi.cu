@@ -51,7 +51,8 @@ struct Prof {
   double ms[PC_NCLS] = {};
   long long calls[PC_NCLS] = {};
   long long kernels[PC_NCLS] = {};
-  double bytes[PC_NCLS] = {};
+  double bytes[PC_NCLS] = {};        // algorithmic bytes (what the step must move)
+  double impl_bytes[PC_NCLS] = {};   // this implementation's own byte model (intermediates included)
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, size_t>> pending;   // class, first event index
@@ -165,6 +166,7 @@ struct omm_ctx {
   std::vector<SppPole> spp_poles;
   void* factor = nullptr;
   void* ynd = nullptr;
+  void* xnd = nullptr;    // assembled right-hand sides, then solutions, ND order (S x n)
   void* ubuf = nullptr;
   int* d_node_ns = nullptr;
   int* d_node_nb = nullptr;
@@ -175,6 +177,8 @@ struct omm_ctx {
   long long* d_node_wb = nullptr;
   int* d_perm = nullptr;
   int* d_bnat = nullptr;
+  int* d_bnd = nullptr;
+  int* d_iperm = nullptr;       // natural -> ND index (the Green kernel's store order)
   int* d_cptr = nullptr;
   int* d_cidx = nullptr;
   int* d_fblocks = nullptr;
@@ -189,10 +193,12 @@ struct omm_ctx {
   int* d_lunk = nullptr;                    // unknowns of each tree height (ND indices)
   // algorithmic complex elements of the triangular-solve phases: per system and per pole
   double tb_leaf_fwd_sys = 0, tb_leaf_bwd_sys = 0, tb_leaf_pole = 0, tb_lvl_sys = 0, tb_lvl_pole = 0;
+  double n_leaf = 0, n_sep = 0;   // unknowns in the leaves / in the separators (algorithmic bytes)
   long long nact_last = -1;   // systems active after the last count (-1: unknown); algorithmic bytes
                               // of masked launches count these only
   std::vector<int> lunk_start, lunk_count;
   size_t trsv_smem = 0;
+  double cur_rtol = 0.0;       // GMRES tolerance of the current round (gmres_rtol, then refilter_rtol)
   int last_gmres_max = 0;
   double last_relres_max = 0.0;
   int gmres_total = 0;
@@ -288,10 +294,11 @@ struct ProfScope {
   omm_ctx* h;
   int cls;
   size_t ev = (size_t)-1;
-  ProfScope(omm_ctx* h_, int cls_, double bytes, int nk) : h(h_), cls(cls_) {
+  ProfScope(omm_ctx* h_, int cls_, double bytes, int nk, double impl = -1.0) : h(h_), cls(cls_) {
     h->prof.calls[cls] += 1;
     h->prof.kernels[cls] += nk;
     h->prof.bytes[cls] += bytes;
+    h->prof.impl_bytes[cls] += impl >= 0.0 ? impl : bytes;
     if (h->prof.on) {
       ev = h->prof_event_pair();
       cudaEventRecord(h->prof.pool[ev], h->st);
@@ -308,6 +315,12 @@ struct ProfScope {
   do {                                             \
     ProfScope _ps(h, (cls), (double)(bytes), (nk)); \
     OMM_TRY(expr);                                 \
+  } while (0)
+// the same with the implementation's own byte count beside the algorithmic one
+#define PROF2(cls, bytes, impl, nk, expr)                            \
+  do {                                                               \
+    ProfScope _ps(h, (cls), (double)(bytes), (nk), (double)(impl)); \
+    OMM_TRY(expr);                                                   \
   } while (0)
 
 double kinetic_max(int dim, int m, double L) {
@@ -351,20 +364,21 @@ omm_status happly(omm_ctx* h, const void* X, void* Y, int ncols, const double2* 
 }
 
 omm_status greenq(omm_ctx* h, const void* B, void* Out, int ncols, int nq, int cpg, const int* active,
-                  const void* ghat = nullptr, const void* q = nullptr) {
+                  const void* ghat = nullptr, const void* q = nullptr, const int* iperm = nullptr) {
   if (!ghat) ghat = h->ghat;
   if (!q) q = h->qd;
   const double bytes = (2.0 * live_cols(h, ncols, active) + (double)((ncols + cpg - 1) / cpg)) * h->csz * (double)h->n;
   if (fused_fft_supported(h->dim, h->m, h->dbl)) {
     PROF(PC_GREENQ, bytes, 1,
-         cuda_status(launch_greenq(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, h->st),
+         cuda_status(launch_greenq(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, iperm, h->st),
                      "greenq"));
     return OMM_OK;
   }
   OMM_TRY(ensure_fft_tmp(h, ncols, h->dbl));
   PROF(PC_GREENQ, bytes, big_fft_launches(h->dim, h->m, h->dbl, true),
        cuda_status(
-           launch_greenq_big(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, h->fft_tmp, h->st),
+           launch_greenq_big(h->dbl, h->dim, h->m, B, Out, ncols, ghat, q, nq, cpg, h->tw, active, iperm, h->fft_tmp,
+                             h->st),
            "greenq"));
   return OMM_OK;
 }
@@ -455,6 +469,7 @@ TrsvArgs trsv_args(omm_ctx* h, int Ncols, size_t S) {
   a.node_wb = h->d_node_wb;
   a.perm = h->d_perm;
   a.bnat = h->d_bnat;
+  a.bnd = h->d_bnd;
   a.contrib_ptr = h->d_cptr;
   a.contrib_idx = h->d_cidx;
   a.factor_size = h->spp.factor_size;
@@ -509,7 +524,8 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
     return cuda_status(cudaMemcpyAsync(Z, Vk, S * h->n * h->csz, cudaMemcpyDeviceToDevice, h->st), "copy");
   }
   if (inner == OMM_INNER_KINETIC) return greenq(h, Vk, Z, (int)S, 1, Ncols, active);
-  OMM_TRY(greenq(h, Vk, tmp, (int)S, h->nq, Ncols, active));
+  // Green kernel + Q stencil, stored in the nested-dissection order of the solves
+  OMM_TRY(greenq(h, Vk, tmp, (int)S, h->nq, Ncols, active, nullptr, nullptr, h->d_iperm));
   TrsvArgs a = trsv_args(h, Ncols, S);
   TrsvLevels lv = trsv_levels(h);
   const LeafArgs la = leaf_args(h, 0);
@@ -532,8 +548,8 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   }
   auto spp = [&](int phases) -> omm_status {
     if (ng == 1)
-      return cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, P, tmp, h->ynd, h->ubuf, Z, h->factor, active,
-                                          h->trsv_smem, h->st),
+      return cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, P, tmp, h->ynd, h->ubuf, Z, h->xnd, h->factor,
+                                          active, h->trsv_smem, h->st),
                          "spp");
     OMM_TRY(cuda_status(cudaEventRecord(h->ev_fork, h->st), "fork"));
     int p0 = 0;
@@ -545,6 +561,7 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
       OMM_TRY(cuda_status(
           launch_spp_solve(phases, h->dbl, a, lv, leaf_args(h, p0), pg, (const char*)tmp + vec0,
                            (char*)h->ynd + vec0, (char*)h->ubuf + sys0 * h->csz, (char*)Z + vec0,
+                           (char*)h->xnd + vec0,
                            (const char*)h->factor + (size_t)p0 * h->spp.factor_size * h->csz,
                            active ? active + sys0 : nullptr, h->trsv_smem, h->st2[g]),
           "spp"));
@@ -555,11 +572,19 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
     return OMM_OK;
   };
   const int ns = ng;   // launches per kernel (one per stream)
+  // Algorithmic bytes of the triangular solves (L then U): each unknown's right-hand side
+  // read and y written, y read and x written (4 per unknown and active system), and each
+  // pole's factor read once (leaf values split over the two leaf passes).  The
+  // implementation's own model adds the update rows, the assembled separator right-hand
+  // sides and the boundary gathers.
   if (has_leaves)
-    PROF(PC_TRSV_LEAF, (h->tb_leaf_fwd_sys * Se + h->tb_leaf_pole * P) * cs, ns, spp(SPP_LEAF_FWD));
-  PROF(PC_TRSV, (h->tb_lvl_sys * Se + h->tb_lvl_pole * P) * cs, ns * nk, spp(SPP_LEVELS_FWD | SPP_LEVELS_BWD));
+    PROF2(PC_TRSV_LEAF, (2.0 * h->n_leaf * Se + 0.5 * h->tb_leaf_pole * P) * cs,
+          (h->tb_leaf_fwd_sys * Se + h->tb_leaf_pole * P) * cs, ns, spp(SPP_LEAF_FWD));
+  PROF2(PC_TRSV, (4.0 * h->n_sep * Se + h->tb_lvl_pole * P) * cs, (h->tb_lvl_sys * Se + h->tb_lvl_pole * P) * cs,
+        ns * nk, spp(SPP_LEVELS_FWD | SPP_LEVELS_BWD));
   if (has_leaves)
-    PROF(PC_TRSV_LEAF, (h->tb_leaf_bwd_sys * Se + h->tb_leaf_pole * P) * cs, ns, spp(SPP_LEAF_BWD));
+    PROF2(PC_TRSV_LEAF, (2.0 * h->n_leaf * Se + 0.5 * h->tb_leaf_pole * P) * cs,
+          (h->tb_leaf_bwd_sys * Se + h->tb_leaf_pole * P) * cs, ns, spp(SPP_LEAF_BWD));
   return OMM_OK;
 }
 
@@ -582,7 +607,7 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
   const size_t vs = (size_t)d.S * h->n * h->csz;
   auto Vk = [&](int k) { return (void*)((char*)h->Vb + (size_t)k * vs); };
   auto Zk = [&](int k) { return (void*)((char*)h->Zb + (size_t)k * vs); };
-  const double rtol = h->prm.gmres_rtol;
+  const double rtol = h->cur_rtol;
   const int fixed = h->prm.gmres_fixed;
   OMM_TRY(cuda_status(cudaMemsetAsync(h->itot, 0, sizeof(int) * d.S, h->st), "memset"));
   for (int cyc = 0; cyc < h->prm.gmres_cycles; ++cyc) {
@@ -736,6 +761,8 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
     PROF(PC_BLOCKUPD, 3.0 * cnt * h->csz, 1,
          cuda_status(launch_block_update(h->dbl, h->X(), h->HX(), h->M1, h->M2, 0.0, 2.0, h->N, h->n, h->Grad, h->st),
                      "grad"));
+    PROF(PC_VEC, 1.0 * cnt * h->csz, 2,
+         cuda_status(launch_redot(h->dbl, cnt, h->Grad, h->Grad, &h->sc->grad2, h->red_work, h->st), "dot"));
     OMM_TRY(precondition(h, h->Grad, h->G, -1.0));
     PROF(PC_VEC, 2.0 * cnt * h->csz, 2,
          cuda_status(launch_redot(h->dbl, cnt, h->G, h->G, &h->sc->gg, h->red_work, h->st), "dot"));
@@ -777,15 +804,17 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
       ++it;
       break;
     }
-    if (h->sc_h->converged) {
+    if (h->sc_h->converged && !h->prm.fixed_iters) {
       *conv = true;
       ++it;
       break;
     }
   }
+  if (h->prm.fixed_iters && it == k && !h->breakdown) *conv = true;   // the fixed schedule ran out
   *done_iters = it;
   if (st) {
     st->energy = h->sc_h->E1;
+    st->grad_norm = std::sqrt(std::max(h->sc_h->grad2, 0.0));
     st->gmres_iters_max = h->last_gmres_max;
     st->gmres_relres_max = h->last_relres_max;
     st->gmres_iters_total = h->gmres_total;
@@ -794,21 +823,40 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
 }
 
 
-// FP64 energy E_omm and residual ||HX - X S^-1 K||_F / ||X||_F of the current X (shift
-// invariant; divided by the spectral gap it bounds the subspace angle, Davis-Kahan):
-// X converted to complex double, FP64 H-apply (shift sigma) and FP64 Grams.
-omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
+// FP64 check of the current X, all on the device: X converted to complex128, FP64 H-apply
+// (shift sigma) and FP64 Gram C = X^*[X HX]; one CTA forms E_omm = tr K - 1/2 tr(S K)
+// (eq. omm), the Cholesky factor S = R^* R and R^-1, two small products give -S^-1 K, and
+// FP64 block updates form the Rayleigh-Ritz residual Res = HX - X S^-1 K (shift
+// invariant) and the residual of the orthonormal basis Q = X R^-1 of span X,
+// Res R^-1 = HQ - Q (Q^* H Q).  Outputs: *E; *resid = ||Res||_F / ||X||_F; *resid_orth =
+// ||Res R^-1||_F (divided by the spectral gap it bounds the sine of the largest angle to
+// the exact invariant subspace, Davis-Kahan).  A non-positive Cholesky pivot (X rank
+// deficient) leaves both residuals NaN.
+omm_status energy_fp64(omm_ctx* h, double* E, double* resid, double* resid_orth = nullptr) {
   const int N = h->N;
   const size_t cnt = (size_t)N * h->n;
+  const size_t nn = (size_t)N * N;
   if (!h->fp64_ready) {
-    OMM_TRY(h->dalloc(&h->X64, cnt * 16 * 3));   // [X | HX | R] in FP64
+    OMM_TRY(h->dalloc(&h->X64, cnt * 16 * 4));   // [X | HX | Res | Res R^-1] in FP64
     OMM_TRY(h->dalloc_t(&h->gram64, (size_t)N * 2 * N * sizeof(double2)));
     OMM_TRY(h->dalloc(&h->gram64_work, gram_work_bytes(N, 2 * N, h->n)));
     OMM_TRY(h->dalloc_t(&h->tmp_shift, sizeof(double2) * 2));
+    // N x N: R, R^-1, T, -S^-1 K, zeros; then E, three norms, the Cholesky flag
+    OMM_TRY(h->dalloc(&h->m64, 5 * nn * 16 + 4 * sizeof(double) + sizeof(int)));
+    OMM_TRY(cuda_status(cudaMemsetAsync((char*)h->m64 + 4 * nn * 16, 0, nn * 16, h->st), "memset"));
     h->fp64_ready = true;
   }
   void* X64 = h->X64;
   void* HX64 = (char*)h->X64 + cnt * 16;
+  void* R64 = (char*)h->X64 + 2 * cnt * 16;
+  void* Q64 = (char*)h->X64 + 3 * cnt * 16;
+  double2* Rc = (double2*)h->m64;
+  double2* Rinv = Rc + nn;
+  double2* T = Rc + 2 * nn;
+  double2* Mneg = Rc + 3 * nn;
+  const double2* Z0 = Rc + 4 * nn;
+  double* dres = (double*)(Rc + 5 * nn);   // E, |Res|^2, |X|^2, |Res R^-1|^2
+  int* dok = (int*)(dres + 4);
   if (h->dbl)
     OMM_TRY(cuda_status(cudaMemcpyAsync(X64, h->X(), cnt * 16, cudaMemcpyDeviceToDevice, h->st), "copy"));
   else
@@ -818,70 +866,26 @@ omm_status energy_fp64(omm_ctx* h, double* E, double* resid) {
   OMM_TRY(happly(h, X64, HX64, N, h->tmp_shift, N, nullptr, true));
   PROF(PC_GRAM, 3.0 * cnt * 16, 2,
        cuda_status(launch_gram(true, X64, N, X64, 2 * N, h->n, h->gram64, 2 * N, h->gram64_work, h->st), "gram64"));
-  std::vector<double2> C((size_t)N * 2 * N);
-  OMM_TRY(cuda_status(cudaMemcpyAsync(C.data(), h->gram64, C.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->st),
-                      "gram64 d2h"));
-  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
-  // E = 1/2 tr((2I - S) K) = tr K - 1/2 tr(S K)
-  double trK = 0.0, trSK = 0.0;
-  for (int i = 0; i < N; ++i) {
-    trK += C[(size_t)i * 2 * N + N + i].x;
-    for (int j = 0; j < N; ++j) {
-      const double2 s = C[(size_t)i * 2 * N + j], k = C[(size_t)j * 2 * N + N + i];
-      trSK += s.x * k.x - s.y * k.y;
-    }
-  }
-  *E = trK - 0.5 * trSK;
+  PROF(PC_SMALL, 0, 3,
+       cuda_status(launch_fp64_check_small(h->gram64, 2 * N, N, dres, Rc, Rinv, T, Mneg, dok, h->st), "fp64 small"));
   if (resid) {
-    // R = HX - X (S^-1 K) formed explicitly in FP64 (Rayleigh-Ritz residual), then |R|_F / |X|_F
-    std::vector<cd> S((size_t)N * N), K((size_t)N * N);
-    for (int i = 0; i < N; ++i)
-      for (int j = 0; j < N; ++j) {
-        const double2 sv = C[(size_t)i * 2 * N + j], kv = C[(size_t)i * 2 * N + N + j];
-        S[(size_t)i * N + j] = cd(sv.x, sv.y);
-        K[(size_t)i * N + j] = cd(kv.x, kv.y);
-      }
-    // solve S Y = K by Gaussian elimination with partial pivoting (N x N, host)
-    std::vector<cd> A(S), Y(K);
-    for (int c = 0; c < N; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < N; ++r)
-        if (std::abs(A[(size_t)r * N + c]) > std::abs(A[(size_t)piv * N + c])) piv = r;
-      if (piv != c)
-        for (int j = 0; j < N; ++j) {
-          std::swap(A[(size_t)c * N + j], A[(size_t)piv * N + j]);
-          std::swap(Y[(size_t)c * N + j], Y[(size_t)piv * N + j]);
-        }
-      const cd d = A[(size_t)c * N + c];
-      for (int r = c + 1; r < N; ++r) {
-        const cd f = A[(size_t)r * N + c] / d;
-        if (f == cd(0.0, 0.0)) continue;
-        for (int j = c; j < N; ++j) A[(size_t)r * N + j] -= f * A[(size_t)c * N + j];
-        for (int j = 0; j < N; ++j) Y[(size_t)r * N + j] -= f * Y[(size_t)c * N + j];
-      }
-    }
-    for (int c = N - 1; c >= 0; --c)
-      for (int j = 0; j < N; ++j) {
-        cd sacc = Y[(size_t)c * N + j];
-        for (int k = c + 1; k < N; ++k) sacc -= A[(size_t)c * N + k] * Y[(size_t)k * N + j];
-        Y[(size_t)c * N + j] = sacc / A[(size_t)c * N + c];
-      }
-    std::vector<cd> Mh((size_t)2 * N * N, cd(0.0, 0.0));   // [ -Y | 0 ]
-    for (size_t e = 0; e < (size_t)N * N; ++e) Mh[e] = -Y[e];
-    if (!h->m64) OMM_TRY(h->dalloc(&h->m64, (size_t)2 * N * N * 16 + 2 * sizeof(double)));
-    OMM_TRY(cuda_status(cudaMemcpyAsync(h->m64, Mh.data(), Mh.size() * 16, cudaMemcpyHostToDevice, h->st), "M"));
-    void* R64 = (char*)h->X64 + 2 * cnt * 16;
-    const double2* M1 = (const double2*)h->m64;
-    const double2* M2 = M1 + (size_t)N * N;
-    double* nrm = (double*)((char*)h->m64 + (size_t)2 * N * N * 16);
     PROF(PC_BLOCKUPD, 3.0 * cnt * 16, 1,
-         cuda_status(launch_block_update(true, X64, HX64, M1, M2, 0.0, 1.0, N, h->n, R64, h->st), "resid"));
-    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, R64, R64, nrm, h->red_work, h->st), "dot"));
-    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, X64, X64, nrm + 1, h->red_work, h->st), "dot"));
-    double nr[2] = {0.0, 0.0};
-    OMM_TRY(cuda_status(cudaMemcpyAsync(nr, nrm, sizeof(nr), cudaMemcpyDeviceToHost, h->st), "d2h"));
-    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
-    *resid = std::sqrt(nr[0] / std::max(nr[1], 1e-300));
+         cuda_status(launch_block_update(true, X64, HX64, Mneg, Z0, 0.0, 1.0, N, h->n, R64, h->st), "resid"));
+    PROF(PC_BLOCKUPD, 2.0 * cnt * 16, 1,
+         cuda_status(launch_block_update(true, R64, R64, Rinv, Z0, 0.0, 0.0, N, h->n, Q64, h->st), "resid orth"));
+    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, R64, R64, dres + 1, h->red_work, h->st), "dot"));
+    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, X64, X64, dres + 2, h->red_work, h->st), "dot"));
+    PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, Q64, Q64, dres + 3, h->red_work, h->st), "dot"));
+  }
+  double out[4] = {0.0, 0.0, 0.0, 0.0};
+  int ok = 0;
+  OMM_TRY(cuda_status(cudaMemcpyAsync(out, dres, sizeof(out), cudaMemcpyDeviceToHost, h->st), "d2h"));
+  OMM_TRY(cuda_status(cudaMemcpyAsync(&ok, dok, sizeof(int), cudaMemcpyDeviceToHost, h->st), "d2h"));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
+  *E = out[0];
+  if (resid) {
+    *resid = ok ? std::sqrt(out[1] / std::max(out[2], 1e-300)) : std::nan("");
+    if (resid_orth) *resid_orth = ok ? std::sqrt(out[3]) : std::nan("");
   }
   return OMM_OK;
 }
@@ -909,6 +913,8 @@ omm_status build_spp(omm_ctx* h) {
     OMM_TRY(upload_vec(h, &h->d_node_wb, wb));
     OMM_TRY(upload_vec(h, &h->d_perm, s.perm));
     OMM_TRY(upload_vec(h, &h->d_bnat, s.bnat));
+    OMM_TRY(upload_vec(h, &h->d_bnd, s.bnd));
+    OMM_TRY(upload_vec(h, &h->d_iperm, s.iperm));
     OMM_TRY(upload_vec(h, &h->d_cptr, s.contrib_ptr));
     OMM_TRY(upload_vec(h, &h->d_cidx, s.contrib_idx));
     OMM_TRY(upload_vec(h, &h->d_fblocks, s.fblocks));
@@ -924,6 +930,8 @@ omm_status build_spp(omm_ctx* h) {
         else { ubs += nd.nb; flv += 2.0 * (double)(nd.ns + nd.nb) * nd.ns; }
       }
       const double nsep = (double)s.n - nl;
+      h->n_leaf = nl;
+      h->n_sep = nsep;
       h->tb_leaf_fwd_sys = 2 * nl + ubl;              // b in, y out, update rows out
       h->tb_leaf_bwd_sys = ubl + 2 * nl;              // halo x in, y in, x out
       h->tb_leaf_pole = (double)s.leaf_size;
@@ -993,6 +1001,9 @@ omm_status omm_default_params(omm_params* p) {
   p->gram_tensor = 0;
   p->real_orbitals = 0;
   p->trsv_streams = 0;
+  p->fixed_iters = 0;
+  p->refilter_rtol = 0.0;
+  p->gap = 0.0;
   return OMM_OK;
 }
 
@@ -1035,7 +1046,8 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
       (prm.precision != OMM_FP64 && prm.precision != OMM_MIXED) || prm.inner < 0 || prm.inner > 2 ||
       prm.stencil_radius != 1 || prm.trsv_streams < 0 || prm.trsv_streams > omm_ctx::kTrsvStreams ||
       !(prm.gmres_rtol >= 0.0) || !std::isfinite(prm.gmres_rtol) || !(prm.tol >= 0.0) || !std::isfinite(prm.tol) ||
-      !(prm.pivot_floor >= 0.0) || !std::isfinite(prm.pivot_floor) || !std::isfinite(shift))
+      !(prm.pivot_floor >= 0.0) || !std::isfinite(prm.pivot_floor) || !std::isfinite(shift) || prm.fixed_iters < 0 ||
+      !(prm.refilter_rtol >= 0.0) || !std::isfinite(prm.refilter_rtol) || !(prm.gap >= 0.0) || !std::isfinite(prm.gap))
     return OMM_EINVAL;
   const bool dbl = prm.precision == OMM_FP64;
   if (!fused_fft_supported(g->dim, m, dbl) && !big_fft_supported(g->dim, m)) return OMM_EUNSUPPORTED;
@@ -1062,6 +1074,7 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
   h->shift = shift;
   h->kin = 2.0 * M_PI * M_PI / (g->box_len * g->box_len);
   h->prm = prm;
+  h->cur_rtol = prm.gmres_rtol;
   h->dbl = dbl;
   h->csz = dbl ? 16 : 8;
   h->st = (cudaStream_t)stream;
@@ -1217,6 +1230,10 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
         OMM_TRY(h->dalloc(&h->leafvals, (size_t)P * h->spp.leaf_size * h->csz));
         OMM_TRY(h->dalloc(&h->ubuf, (size_t)h->spp.urows * P * h->N * h->csz));
         OMM_TRY(h->dalloc(&h->ynd, (size_t)P * h->N * n * h->csz));
+        OMM_TRY(h->dalloc(&h->xnd, (size_t)P * h->N * n * h->csz));
+        // the backward products of systems masked off read xnd entries nothing wrote:
+        // keep them finite
+        OMM_TRY(cuda_status(cudaMemsetAsync(h->xnd, 0, (size_t)P * h->N * n * h->csz, h->st), "memset"));
         h->Pfac = P;
       }
       std::vector<cd> fall((size_t)P * fs);
@@ -1295,23 +1312,32 @@ omm_status omm_solve(omm_t h, omm_stats* st) {
   // gTPA is no spectral filter: one CG round from the orbitals as given (Sec. 4's runs
   // of the TPA-type preconditioners start from the initial guess)
   const int rounds = h->use_gtpa ? 0 : h->prm.refilter;
+  const int kmax = h->prm.fixed_iters > 0 ? h->prm.fixed_iters : h->prm.maxit;
+  omm_status rs = OMM_OK;
   for (int round = 0; round <= rounds; ++round) {
+    // the first round at gmres_rtol, the refilter rounds at refilter_rtol
+    h->cur_rtol = (round > 0 && h->prm.refilter_rtol > 0.0) ? h->prm.refilter_rtol : h->prm.gmres_rtol;
     if (!h->use_gtpa) {
-      OMM_TRY(omm_filter(h));
+      rs = omm_filter(h);
+      if (rs != OMM_OK) break;
       loc.filters++;
     }
     int done = 0;
-    OMM_TRY(cg_steps(h, h->prm.maxit, &loc, &done, &conv));
+    rs = cg_steps(h, kmax, &loc, &done, &conv);
     total += done;
-    if (h->breakdown) break;
+    if (rs != OMM_OK || h->breakdown) break;
   }
+  h->cur_rtol = h->prm.gmres_rtol;
+  OMM_TRY(rs);
   loc.iters = total;
   loc.converged = conv;
-  double E = 0.0, r = 0.0;
-  omm_status s = energy_fp64(h, &E, &r);
+  double E = 0.0, r = 0.0, ro = 0.0;
+  omm_status s = energy_fp64(h, &E, &r, &ro);
   if (s == OMM_OK) {
     loc.energy_fp64 = E;
     loc.resid_fp64 = r;
+    loc.resid_orth = ro;
+    loc.angle_bound = h->prm.gap > 0.0 ? ro / h->prm.gap : 0.0;
   } else if (s != OMM_EUNSUPPORTED) {
     return s;
   }
@@ -1381,12 +1407,12 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
   // one pole, ncols systems: Green + stencil into the GMRES scratch, then the solves
   const size_t n = h->n;
   OMM_TRY(greenq(h, B, h->tv, ncols, h->nq, ncols, nullptr, (char*)h->ghat + (size_t)pole * n * h->csz,
-                 (char*)h->qd + (size_t)pole * h->nq * h->csz));
+                 (char*)h->qd + (size_t)pole * h->nq * h->csz, h->d_iperm));
   TrsvArgs a = trsv_args(h, ncols, (size_t)ncols);
   TrsvLevels lv = trsv_levels(h);
   const void* f = (char*)h->factor + (size_t)pole * h->spp.factor_size * h->csz;
-  OMM_TRY(cuda_status(launch_spp_solve(SPP_ALL, h->dbl, a, lv, leaf_args(h, pole), 1, h->tv, h->ynd, h->ubuf, U, f, nullptr,
-                                       h->trsv_smem, h->st),
+  OMM_TRY(cuda_status(launch_spp_solve(SPP_ALL, h->dbl, a, lv, leaf_args(h, pole), 1, h->tv, h->ynd, h->ubuf, U, h->xnd,
+                                       f, nullptr, h->trsv_smem, h->st),
                       "spp"));
   return cuda_status(cudaStreamSynchronize(h->st), "sync");
 }
@@ -1657,7 +1683,7 @@ omm_status omm_factor_info(omm_t h, int pole, int* nsuper, long long* nnz, doubl
 }
 
 omm_status omm_profile_enable(omm_t h, int on) {
-  if (!h) return OMM_EINVAL;
+  if (!h || on < 0 || on > 2) return OMM_EINVAL;
   h->prof_flush();
   if (on) {
     for (int c = 0; c < PC_NCLS; ++c) {
@@ -1665,9 +1691,16 @@ omm_status omm_profile_enable(omm_t h, int on) {
       h->prof.calls[c] = 0;
       h->prof.kernels[c] = 0;
       h->prof.bytes[c] = 0.0;
+      h->prof.impl_bytes[c] = 0.0;
     }
   }
-  h->prof.on = on != 0;
+  h->prof.on = on == 1;
+  return OMM_OK;
+}
+
+omm_status omm_profile_read_impl(omm_t h, int cls, double* impl_bytes) {
+  if (!h || !impl_bytes || cls < 0 || cls >= PC_NCLS) return OMM_EINVAL;
+  *impl_bytes = h->prof.impl_bytes[cls];
   return OMM_OK;
 }
 

@@ -2,6 +2,8 @@
 //
 //  happly : Y = F^-1 (T(k) F x) + (V - s_g) x     (Sec. 4 eq. ex1mat; shifted for eq. lst)
 //  greenq : out = Q (F^-1 (Ghat_g(k) F b))          (Sec. 3.2 eqs. GLu / QG: Q (G b))
+//           optionally stored through a permutation (out[iperm[i]]), e.g. straight into the
+//           nested-dissection order of the triangular solves that consume it
 //
 // s_g / Ghat_g / q_g depend on the column group g = col / cols_per_group (one group per
 // pole when the columns of all P shifted systems are batched).  T(k) = c |k|^2 with the
@@ -67,7 +69,7 @@ template <typename T, int M, int D>
 __global__ void __launch_bounds__(GridCfg<T, M, D>::NT)
 greenq_kernel(const cx_t<T>* __restrict__ B, cx_t<T>* __restrict__ Out, const cx_t<T>* __restrict__ ghat,
               const cx_t<T>* __restrict__ q, int nq, int cols_per_group, const cx_t<T>* __restrict__ tw,
-              const int* __restrict__ active) {
+              const int* __restrict__ active, const int* __restrict__ iperm) {
   using C = cx_t<T>;
   using G = GridCfg<T, M, D>;
   using LY = typename G::LY;
@@ -105,7 +107,7 @@ greenq_kernel(const cx_t<T>* __restrict__ B, cx_t<T>* __restrict__ Out, const cx
           const int xx = (ix + dx + M) % M, yy = (iy + dy + M) % M, zz = (D == 3) ? (iz + dz + M) % M : 0;
           acc = cfma(qs[qi], s[LY::at(xx, yy, zz)], acc);
         }
-    o[i] = acc;
+    o[iperm ? iperm[i] : i] = acc;
   }
 }
 
@@ -124,13 +126,13 @@ static cudaError_t launch_happly_t(const void* X, void* Y, int ncols, const void
 
 template <typename T, int M, int D>
 static cudaError_t launch_greenq_t(const void* B, void* Out, int ncols, const void* ghat, const void* q, int nq,
-                                   int cpg, const void* tw, const int* active, cudaStream_t st) {
+                                   int cpg, const void* tw, const int* active, const int* iperm, cudaStream_t st) {
   using G = GridCfg<T, M, D>;
   auto k = greenq_kernel<T, M, D>;
   cudaError_t e = raise_smem_limit((const void*)k);
   if (e != cudaSuccess) return e;
   k<<<ncols, G::NT, G::smem, st>>>((const cx_t<T>*)B, (cx_t<T>*)Out, (const cx_t<T>*)ghat, (const cx_t<T>*)q, nq,
-                                   cpg, (const cx_t<T>*)tw, active);
+                                   cpg, (const cx_t<T>*)tw, active, iperm);
   return cudaGetLastError();
 }
 
@@ -187,21 +189,22 @@ cudaError_t launch_happly(bool dbl, int dim, int m, const void* X, void* Y, int 
 }
 
 cudaError_t launch_greenq(bool dbl, int dim, int m, const void* B, void* Out, int ncols, const void* ghat,
-                          const void* q, int nq, int cpg, const void* tw, const int* active, cudaStream_t st) {
+                          const void* q, int nq, int cpg, const void* tw, const int* active, const int* iperm,
+                          cudaStream_t st) {
   if (ncols <= 0) return cudaSuccess;
 #define C2_(M)                                                                                        \
   case M:                                                                                             \
-    return dbl ? launch_greenq_t<double, M, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st)              \
-               : launch_greenq_t<float, M, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st);
+    return dbl ? launch_greenq_t<double, M, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, st)              \
+               : launch_greenq_t<float, M, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, st);
 #define C3_(M)                                                                                        \
   case M:                                                                                             \
-    return dbl ? launch_greenq_t<double, M, 3>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st)              \
-               : launch_greenq_t<float, M, 3>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st);
+    return dbl ? launch_greenq_t<double, M, 3>(B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, st)              \
+               : launch_greenq_t<float, M, 3>(B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, st);
   if (dim == 2) {
     switch (m) {
       OMM_GRID_CASES_2D(C2_)
       case 128:
-        if (!dbl) return launch_greenq_t<float, 128, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, st);
+        if (!dbl) return launch_greenq_t<float, 128, 2>(B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, st);
         break;
       default: break;
     }

@@ -193,10 +193,12 @@ static cudaError_t launch_xyslab(const cx_t<T>* in, cx_t<T>* out, size_t n, int 
   return cudaGetLastError();
 }
 
-// ---- Q stencil on a natural-order grid function: out[j] = sum_t q_t in[j + o_t]
+// ---- Q stencil on a natural-order grid function: out[j] = sum_t q_t in[j + o_t], stored at
+// out[iperm[j]] when a permutation is given
 template <typename T>
 __global__ void stencil_kernel(const cx_t<T>* __restrict__ in, cx_t<T>* __restrict__ out, int dim, int m, size_t n,
-                               const cx_t<T>* __restrict__ q, int nq, int cpg, const int* __restrict__ active) {
+                               const cx_t<T>* __restrict__ q, int nq, int cpg, const int* __restrict__ active,
+                               const int* __restrict__ iperm) {
   using C = cx_t<T>;
   const int col = blockIdx.y;
   if (active && !active[col]) return;
@@ -214,7 +216,7 @@ __global__ void stencil_kernel(const cx_t<T>* __restrict__ in, cx_t<T>* __restri
           const int xx = (ix + dx + m) % m, yy = (iy + dy + m) % m, zz = (dim == 3) ? (iz + dz + m) % m : 0;
           acc = cfma(qs[qi], g[xx + (size_t)m * (yy + (size_t)m * zz)], acc);
         }
-    out[(size_t)col * n + i] = acc;
+    out[(size_t)col * n + (iperm ? (size_t)iperm[i] : i)] = acc;
   }
 }
 
@@ -250,7 +252,8 @@ static cudaError_t happly_big_t(int dim, const void* X, void* Y, int ncols, cons
 
 template <typename T, int M>
 static cudaError_t greenq_big_t(int dim, const void* B, void* Out, int ncols, const void* ghat, const void* q, int nq,
-                                int cpg, const void* tw, const int* active, void* tmp, cudaStream_t st) {
+                                int cpg, const void* tw, const int* active, const int* iperm, void* tmp,
+                                cudaStream_t st) {
   using C = cx_t<T>;
   const size_t n = (dim == 3) ? (size_t)M * M * M : (size_t)M * M;
   const int xt = (int)(n / M / RX);
@@ -265,7 +268,7 @@ static cudaError_t greenq_big_t(int dim, const void* B, void* Out, int ncols, co
     lpass_kernel<T, M, 3, 2, 3><<<ncols * lt, BT, 0, st>>>(w, n, t, 0.0, gh, cpg, active, lt);
     e = launch_xyslab<T, M, 2>(w, w, n, ncols, t, nullptr, nullptr, nullptr, 1, active, st);
     if (e != cudaSuccess) return e;
-    stencil_kernel<T><<<dim3(sb, ncols), 256, 0, st>>>(w, (C*)Out, dim, M, n, (const C*)q, nq, cpg, active);
+    stencil_kernel<T><<<dim3(sb, ncols), 256, 0, st>>>(w, (C*)Out, dim, M, n, (const C*)q, nq, cpg, active, iperm);
     return cudaGetLastError();
   }
   xpass_kernel<T, M, 0><<<ncols * xt, BT, 0, st>>>((const C*)B, w, n, t, nullptr, nullptr, nullptr, 1, active, xt);
@@ -277,7 +280,7 @@ static cudaError_t greenq_big_t(int dim, const void* B, void* Out, int ncols, co
     lpass_kernel<T, M, 3, 1, 1><<<ncols * lt, BT, 0, st>>>(w, n, t, 0.0, gh, cpg, active, lt);
   }
   xpass_kernel<T, M, 2><<<ncols * xt, BT, 0, st>>>(w, w, n, t, nullptr, nullptr, nullptr, 1, active, xt);
-  stencil_kernel<T><<<dim3(sb, ncols), 256, 0, st>>>(w, (C*)Out, dim, M, n, (const C*)q, nq, cpg, active);
+  stencil_kernel<T><<<dim3(sb, ncols), 256, 0, st>>>(w, (C*)Out, dim, M, n, (const C*)q, nq, cpg, active, iperm);
   return cudaGetLastError();
 }
 
@@ -314,13 +317,13 @@ cudaError_t launch_happly_big(bool dbl, int dim, int m, const void* X, void* Y, 
 }
 
 cudaError_t launch_greenq_big(bool dbl, int dim, int m, const void* B, void* Out, int ncols, const void* ghat,
-                              const void* q, int nq, int cpg, const void* tw, const int* active, void* tmp,
-                              cudaStream_t st) {
+                              const void* q, int nq, int cpg, const void* tw, const int* active, const int* iperm,
+                              void* tmp, cudaStream_t st) {
   if (ncols <= 0) return cudaSuccess;
 #define C_(M)                                                                                              \
   case M:                                                                                                  \
-    return dbl ? greenq_big_t<double, M>(dim, B, Out, ncols, ghat, q, nq, cpg, tw, active, tmp, st)       \
-               : greenq_big_t<float, M>(dim, B, Out, ncols, ghat, q, nq, cpg, tw, active, tmp, st);
+    return dbl ? greenq_big_t<double, M>(dim, B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, tmp, st)       \
+               : greenq_big_t<float, M>(dim, B, Out, ncols, ghat, q, nq, cpg, tw, active, iperm, tmp, st);
   switch (m) {
     C_(16) C_(32) C_(48) C_(64) C_(96) C_(128)
     default: break;

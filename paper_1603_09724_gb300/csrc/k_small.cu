@@ -242,3 +242,109 @@ cudaError_t launch_gram_to_matrix(bool dbl, const double2* C, int ldc, int N, do
 }
 
 }  // namespace omm
+
+namespace omm {
+
+// ---- FP64 check of a result (once per solve).  From the FP64 Gram C = X^*[X  (H - sigma) X]
+// (N x 2N, row stride ldc): S = C[:, 0:N], K = C[:, N:2N].  One CTA:
+//   E_omm = tr K - 1/2 tr(S K)                              (eq. omm)
+//   S = R^* R (right-looking Cholesky, R upper), then R^-1 by back substitution, one
+//   column per thread.
+// The N x N arrays R, Rinv live in global memory (row-major); every step that reads what
+// other threads wrote follows a __syncthreads, which orders global memory within the CTA.
+// ok[0] = 0 if a pivot of S is not positive (X rank deficient), else 1.
+__global__ void __launch_bounds__(1024) fp64_chol_kernel(const double2* __restrict__ Cg, int ldc, int N,
+                                                          double* __restrict__ E, double2* R, double2* Rinv,
+                                                          int* __restrict__ ok) {
+  __shared__ double sh[32 * 2];
+  __shared__ double dj;
+  __shared__ int good;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double v[2] = {0.0, 0.0};
+  for (int idx = tid; idx < N * N; idx += bd) {
+    const int i = idx / N, j = idx % N;
+    const double2 s = Cg[(size_t)i * ldc + j], k = Cg[(size_t)j * ldc + N + i];
+    if (i == j) v[0] += Cg[(size_t)i * ldc + N + i].x;
+    v[1] += s.x * k.x - s.y * k.y;
+    R[idx] = (j >= i) ? s : make_double2(0.0, 0.0);
+  }
+  block_sum_vec<2>(v, sh);
+  if (tid == 0) {
+    *E = v[0] - 0.5 * v[1];
+    good = 1;
+  }
+  __syncthreads();
+  for (int j = 0; j < N; ++j) {
+    if (tid == 0) {
+      const double d = R[(size_t)j * N + j].x;
+      if (!(d > 0.0)) good = 0;
+      dj = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    for (int k = j + tid; k < N; k += bd) {
+      const double2 r = R[(size_t)j * N + k];
+      R[(size_t)j * N + k] = (k == j) ? make_double2(dj, 0.0) : make_double2(r.x / dj, r.y / dj);
+    }
+    __syncthreads();
+    const int m = N - j - 1;
+    for (int e = tid; e < m * m; e += bd) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k < i) continue;
+      const double2 a = R[(size_t)j * N + i], b = R[(size_t)j * N + k];   // conj(a) * b
+      double2& t = R[(size_t)i * N + k];
+      t.x -= a.x * b.x + a.y * b.y;
+      t.y -= a.x * b.y - a.y * b.x;
+    }
+    __syncthreads();
+  }
+  for (int c = tid; c < N; c += bd) {
+    for (int r = c + 1; r < N; ++r) Rinv[(size_t)r * N + c] = make_double2(0.0, 0.0);
+    Rinv[(size_t)c * N + c] = make_double2(1.0 / R[(size_t)c * N + c].x, 0.0);
+    for (int r = c - 1; r >= 0; --r) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = r + 1; k <= c; ++k) {
+        const double2 a = R[(size_t)r * N + k], b = Rinv[(size_t)k * N + c];
+        acc.x += a.x * b.x - a.y * b.y;
+        acc.y += a.x * b.y + a.y * b.x;
+      }
+      const double d = R[(size_t)r * N + r].x;
+      Rinv[(size_t)r * N + c] = make_double2(-acc.x / d, -acc.y / d);
+    }
+  }
+  if (tid == 0) *ok = good;
+}
+
+// Out = scale * op(A) B for N x N complex double matrices (row-major, row strides lda, ldb,
+// N for Out); op(A) = A^* when CT.  One thread per output entry.
+template <bool CT>
+__global__ void zgemm_small_kernel(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
+                                   double2* __restrict__ Out, int N, double scale) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * N) return;
+  const int i = idx / N, j = idx % N;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = 0; k < N; ++k) {
+    const double2 a = CT ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k];
+    const double2 b = B[(size_t)k * ldb + j];
+    if (CT) {   // conj(a) b
+      acc.x += a.x * b.x + a.y * b.y;
+      acc.y += a.x * b.y - a.y * b.x;
+    } else {
+      acc.x += a.x * b.x - a.y * b.y;
+      acc.y += a.x * b.y + a.y * b.x;
+    }
+  }
+  Out[idx] = make_double2(scale * acc.x, scale * acc.y);
+}
+
+cudaError_t launch_fp64_check_small(const double2* C, int ldc, int N, double* E, double2* R, double2* Rinv,
+                                    double2* T, double2* Mneg, int* ok, cudaStream_t st) {
+  fp64_chol_kernel<<<1, 1024, 0, st>>>(C, ldc, N, E, R, Rinv, ok);
+  const int nb = (N * N + 255) / 256;
+  // T = R^-* K, then -S^-1 K = -R^-1 T  (S^-1 = R^-1 R^-*)
+  zgemm_small_kernel<true><<<nb, 256, 0, st>>>(Rinv, N, C + N, ldc, T, N, 1.0);
+  zgemm_small_kernel<false><<<nb, 256, 0, st>>>(Rinv, N, T, N, Mneg, N, -1.0);
+  return cudaGetLastError();
+}
+
+}  // namespace omm

@@ -2,7 +2,12 @@
 // (Sec. 3.2: the preconditioned vector is P^-1 Q G b, and P is factored by a sparse
 // direct method in nested-dissection order).  Unknowns are numbered in ND postorder;
 // supernode s owns the contiguous range [off, off + ns) and couples to the ancestor
-// unknowns B(s).
+// unknowns B(s).  The right-hand side b arrives in ND order (the Green kernel stores it
+// so), and every intermediate vector stays in ND order: y in ynd, the assembled
+// separator right-hand sides and then the solution in xnd.  So every gather of the
+// solves reads contiguous runs (a supernode's range, or the pieces of ancestor
+// separators that form B(s)); only the final solution is also scattered into natural
+// order (x) for the operators that follow.
 //
 // With W_f = [L_SS^-1 ; L_BS L_SS^-1] and W_b = [U_SS^-1 , -U_SS^-1 U_SB] (built on the
 // host) every supernode step is one dense complex product over a tile of right-hand
@@ -31,10 +36,10 @@ constexpr int KT = 16;   // k step of the product
 // Forward right-hand sides of one tree height: r_S = b_S - (sum of the update rows of the
 // descendants that target S, in CSR order), for every unknown of the height and every
 // active system of the launch (nsys = its poles x N; u rows have stride a.S, the systems of
-// all poles), written in ND order into x (x is not read before the backward sweep,
-// which overwrites every entry of an active system).  An AS_I x 32 tile (unknowns x
-// systems, one element per thread) is transposed through shared memory so that the gather
-// of b and the store into x run unknown-fastest while the update rows are read
+// all poles), written in ND order into xnd (the backward sweep later overwrites every
+// entry of an active system with the solution).  An AS_I x 32 tile (unknowns x
+// systems, one element per thread) is transposed through shared memory so that the
+// reads of b and the store into xnd run unknown-fastest while the update rows are read
 // system-fastest.  Small tiles: the top heights have few unknowns, and each element waits
 // on a chain of loads, so the grid needs many CTAs.
 constexpr int AS_I = 8;
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const i
     const int ii = t % AS_I, ss = t / AS_I;   // unknown fastest
     const int i = i0 + ii;
     const size_t s = s0 + ss;
-    if (i < cnt && s < nsys && (!active || active[s])) tile[ii][ss] = b[s * a.n + a.perm[lunk[i]]];
+    if (i < cnt && s < nsys && (!active || active[s])) tile[ii][ss] = b[s * a.n + lunk[i]];
   }
   __syncthreads();
   {
@@ -94,6 +99,7 @@ template <typename T, bool FWD, int RBV, int RTV, int NTH>
 __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks,
                                                                const cx_t<T>* __restrict__ b, cx_t<T>* __restrict__ ynd,
                                                                cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
+                                                               cx_t<T>* __restrict__ xnd,
                                                                const cx_t<T>* __restrict__ factor,
                                                                const int* __restrict__ active, int split) {
   using C = cx_t<T>;
@@ -129,10 +135,10 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
       v[q] = mk<C>(0, 0);
       if (idx < K * RT && c < a.N) {
         const size_t s = (size_t)p * a.N + c;
-        if (FWD) {   // assembled by assemble_kernel into x, ND order
-          if (!active || active[s]) v[q] = x[s * a.n + off + i];
-        } else {
-          v[q] = (i < ns) ? ynd[s * a.n + off + i] : x[s * a.n + a.bnat[boff + i - ns]];
+        if (FWD) {   // assembled by assemble_kernel into xnd
+          if (!active || active[s]) v[q] = xnd[s * a.n + off + i];
+        } else {     // y_S, then x_B from the ancestors' solutions (runs in ND order)
+          v[q] = (i < ns) ? ynd[s * a.n + off + i] : xnd[s * a.n + a.bnd[boff + i - ns]];
         }
       }
     }
@@ -214,7 +220,8 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
       if (c >= a.N) continue;
       const size_t s = (size_t)p * a.N + c;
       if (active && !active[s]) continue;
-      x[s * a.n + a.perm[off + r0 + rr]] = Cs[rr][cc];
+      xnd[s * a.n + off + r0 + rr] = Cs[rr][cc];          // for the descendants' gathers
+      x[s * a.n + a.perm[off + r0 + rr]] = Cs[rr][cc];    // the result, natural order
     }
   }
 }
@@ -222,8 +229,8 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
 
 // ---- leaves: banded substitution with the leaf's own L and U (the fill of a leaf stays
 // inside the band of its x-fastest ordering) and sparse couplings to the halo:
-//   forward:  y = L^-1 b_S,  u_s = F_BS (U^-1 y)
-//   backward: x_S = U^-1 (y_S - L^-1 (F_SB x_B))
+//   forward:  y = L^-1 b_S,  u_s = F_BS (U^-1 y)       (b_S: a contiguous ND range)
+//   backward: x_S = U^-1 (y_S - L^-1 (F_SB x_B))      (x_B from xnd, x_S stored in natural order)
 // A CTA holds LT right-hand sides of one pole and one leaf in shared memory, column cc
 // at y[i * LDY + cc], together with the leaf's factor values and index lists, staged
 // once per CTA.  Global accesses are cooperative, leaf index fastest (a warp touches
@@ -271,7 +278,8 @@ size_t leaf_smem_bytes(int max_ns, int max_nb, int bw) {
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const cx_t<T>* __restrict__ b,
                                                   cx_t<T>* __restrict__ ynd, cx_t<T>* __restrict__ u,
-                                                  cx_t<T>* __restrict__ x, const int* __restrict__ active) {
+                                                  cx_t<T>* __restrict__ x, const cx_t<T>* __restrict__ xnd,
+                                                  const int* __restrict__ active) {
   using C = cx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned char live[LT];
@@ -286,8 +294,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
   C* vs = ys + (size_t)la.max_ns * LDY;                                       // Lb | Ub | Fbs | Fsb
   int* is = reinterpret_cast<int*>(vs + leaf_vals_count(la.max_ns, la.max_nb, bw));
   int* iperm = is;                  // natural index of leaf unknown i
-  int* ibnat = iperm + ns;          // natural index of halo unknown j
-  int* ibs = ibnat + nb;            // F_BS columns (leaf unknowns) per halo row, -1 padded
+  int* ibnd = iperm + ns;           // ND index of halo unknown j
+  int* ibs = ibnd + nb;            // F_BS columns (leaf unknowns) per halo row, -1 padded
   int* isb = ibs + nb * LNB;        // F_SB columns (halo unknowns) per leaf row, -1 padded
   {
     const int c = c0 + tid;
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
     } else {
       const int boff = a.node_boff[node];
       const int* sbi = la.sb_idx + la.ioff_sb[li];
-      for (int j = tid; j < nb; j += LT) ibnat[j] = a.bnat[boff + j];
+      for (int j = tid; j < nb; j += LT) ibnd[j] = a.bnd[boff + j];
       for (int e = tid; e < ns * LNB; e += LT) isb[e] = sbi[e];
     }
   }
@@ -323,7 +331,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
       for (int q = 0; q < LGB; ++q) {
         const int idx = base + q * LT;
         const int i = idx % ns, cc = idx / ns;
-        if (idx < ns * LT && live[cc]) v[q] = b[(s0 + cc) * a.n + iperm[i]];
+        if (idx < ns * LT && live[cc]) v[q] = b[(s0 + cc) * a.n + off + i];
       }
 #pragma unroll
       for (int q = 0; q < LGB; ++q) {
@@ -361,11 +369,11 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
         const int i = idx % ns, cc = idx / ns;
         acc[q] = mk<C>(0, 0);
         if (idx < ns * LT && live[cc]) {
-          const C* xs = x + (s0 + cc) * a.n;
+          const C* xs = xnd + (s0 + cc) * a.n;
 #pragma unroll
           for (int t = 0; t < LNB; ++t) {   // -1 entries trail: same order as a breaking loop
             const int j = isb[i * LNB + t];
-            if (j >= 0) acc[q] = cfma(Fsb[i * LNB + t], xs[ibnat[j]], acc[q]);
+            if (j >= 0) acc[q] = cfma(Fsb[i * LNB + t], xs[ibnd[j]], acc[q]);
           }
         }
       }
@@ -414,8 +422,8 @@ size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb) {
 
 template <typename T, bool FWD, int RBV, int RTV, int NTH>
 static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
-                                const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
-                                cudaStream_t st) {
+                                const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                                const int* active, cudaStream_t st) {
   using C = cx_t<T>;
   auto k = trsv_gemm_kernel<T, FWD, RBV, RTV, NTH>;
   cudaError_t e = raise_smem_limit((const void*)k);
@@ -424,7 +432,7 @@ static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count,
   const int split = (std::min(RB, mmax) + RBV - 1) / RBV;
   const dim3 grid((a.N + RTV - 1) / RTV, count * split, P);
   const size_t sm = std::max((size_t)kmax * RTV, (size_t)RBV * (RTV + 1)) * sizeof(C);
-  k<<<grid, NTH, sm, st>>>(a, blocks, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)factor, active, split);
+  k<<<grid, NTH, sm, st>>>(a, blocks, (const C*)b, (C*)ynd, (C*)u, (C*)x, (C*)xnd, (const C*)factor, active, split);
   return cudaGetLastError();
 }
 
@@ -433,21 +441,21 @@ static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count,
 // 32 x RT/2 tiles where 64 x RT leaves the GPU underfilled, else 64 x RT.
 template <typename T, bool FWD>
 static cudaError_t run_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
-                             const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
-                             cudaStream_t st) {
+                             const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                             const int* active, cudaStream_t st) {
   constexpr int RT = TrsvCfg<T>::RT;
   if (mmax <= 16)
-    return launch_level<T, FWD, 16, RT, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, factor, active, st);
+    return launch_level<T, FWD, 16, RT, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
   const long ctas = (long)count * ((a.N + RT - 1) / RT) * P;
   if (ctas >= 8 * 152 && mmax > 32)
-    return launch_level<T, FWD, 64, RT, 128>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, factor, active, st);
-  return launch_level<T, FWD, 32, RT / 2, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, factor, active, st);
+    return launch_level<T, FWD, 64, RT, 128>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
+  return launch_level<T, FWD, 32, RT / 2, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
 }
 
 template <typename T>
 static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
-                         const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
-                         size_t smem_total, cudaStream_t st) {
+                         const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                         const int* active, size_t smem_total, cudaStream_t st) {
   using C = cx_t<T>;
   (void)smem_total;
   auto leaf_f = leaf_kernel<T, true>;
@@ -460,7 +468,7 @@ static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, co
   const size_t lsm = leaf_smem_bytes<T>(la.max_ns, la.max_nb, la.bw);
   const dim3 lgrid((a.N + LT - 1) / LT, la.nleaves, P);
   if (leaves && (phases & SPP_LEAF_FWD)) {
-    leaf_f<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
+    leaf_f<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)xnd, active);
   }
   for (int h = leaves ? 1 : 0; h < lv.nlevels && (phases & SPP_LEVELS_FWD); ++h) {
     if (lv.fcount[h] == 0) continue;
@@ -468,28 +476,28 @@ static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, co
       const size_t nsys = (size_t)P * a.N;   // systems of this launch (a.S is the row stride of u)
       const dim3 agrid((lv.ucount[h] + AS_I - 1) / AS_I, (unsigned)((nsys + 31) / 32));
       assemble_kernel<T><<<agrid, AS_I * 32, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], nsys, (const C*)b,
-                                                       (const C*)u, (C*)x, active);
+                                                       (const C*)u, (C*)xnd, active);
     }
     cudaError_t e = run_level<T, true>(a, lv.fblocks + 2 * lv.fstart[h], lv.fcount[h], lv.fkmax[h], lv.bkmax[h], P,
-                                       b, ynd, u, x, factor, active, st);
+                                       b, ynd, u, x, xnd, factor, active, st);
     if (e != cudaSuccess) return e;
   }
   for (int h = lv.nlevels - 1; h >= (leaves ? 1 : 0) && (phases & SPP_LEVELS_BWD); --h) {
     if (lv.bcount[h] == 0) continue;
     cudaError_t e = run_level<T, false>(a, lv.bblocks + 2 * lv.bstart[h], lv.bcount[h], lv.bkmax[h], lv.fkmax[h], P,
-                                        b, ynd, u, x, factor, active, st);
+                                        b, ynd, u, x, xnd, factor, active, st);
     if (e != cudaSuccess) return e;
   }
   if (leaves && (phases & SPP_LEAF_BWD))
-    leaf_b<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, active);
+    leaf_b<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)xnd, active);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
-                             const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
-                             size_t smem, cudaStream_t st) {
-  if (dbl) return run_t<double>(phases, a, lv, la, P, b, ynd, u, x, factor, active, smem, st);
-  return run_t<float>(phases, a, lv, la, P, b, ynd, u, x, factor, active, smem, st);
+                             const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                             const int* active, size_t smem, cudaStream_t st) {
+  if (dbl) return run_t<double>(phases, a, lv, la, P, b, ynd, u, x, xnd, factor, active, smem, st);
+  return run_t<float>(phases, a, lv, la, P, b, ynd, u, x, xnd, factor, active, smem, st);
 }
 
 }  // namespace omm

@@ -10,9 +10,10 @@ bool fused_fft_supported(int dim, int m, bool dbl);
 cudaError_t launch_happly(bool dbl, int dim, int m, const void* X, void* Y, int ncols, const void* V,
                           const double2* shifts, int cols_per_group, const void* tw, double kin_over_n,
                           const int* active, cudaStream_t st);
+// iperm: NULL (natural-order output) or n indices: out[iperm[i]] receives grid point i
 cudaError_t launch_greenq(bool dbl, int dim, int m, const void* B, void* Out, int ncols, const void* ghat,
                           const void* q, int nq, int cols_per_group, const void* tw, const int* active,
-                          cudaStream_t st);
+                          const int* iperm, cudaStream_t st);
 
 // ---- k_fft_big.cu: multi-pass (per-axis) kernels for large grids; tmp: ncols * n complex
 bool big_fft_supported(int dim, int m);
@@ -22,8 +23,8 @@ cudaError_t launch_happly_big(bool dbl, int dim, int m, const void* X, void* Y, 
                               const double2* shifts, int cols_per_group, const void* tw, double kin_over_n,
                               const int* active, void* tmp, cudaStream_t st);
 cudaError_t launch_greenq_big(bool dbl, int dim, int m, const void* B, void* Out, int ncols, const void* ghat,
-                              const void* q, int nq, int cols_per_group, const void* tw, const int* active, void* tmp,
-                              cudaStream_t st);
+                              const void* q, int nq, int cols_per_group, const void* tw, const int* active,
+                              const int* iperm, void* tmp, cudaStream_t st);
 
 // ---- k_blas.cu
 // C (na x nb, complex double, row-major, ldc) = A^H B; A, B column blocks of length n (lda = ldb = n).
@@ -63,6 +64,7 @@ struct OmmScalars {
   double beta;        // Polak-Ribiere beta
   double gg, ggp;     // <G_m, G_m>, <G_{m-1}, G_{m-1}>
   double gdot;        // <G_m, G_{m-1}>
+  double grad2;       // ||Grad||_F^2 of the last gradient
   double2 t_c;        // t as complex (for axpby)
   double2 beta_c;     // beta as complex
   double2 one_c;
@@ -79,6 +81,11 @@ cudaError_t launch_line_search(bool dbl, const double2* C, int N, double sigma, 
 // M = scale * C (N x N FP64 Gram with row stride ldc) in the working precision
 cudaError_t launch_gram_to_matrix(bool dbl, const double2* C, int ldc, int N, double scale, void* M, cudaStream_t st);
 cudaError_t launch_pr_beta(OmmScalars* sc, int first, cudaStream_t st);
+// FP64 check (one CTA + two small products): from C = X^*[X (H - sigma)X] (N x 2N, ldc)
+// *E = E_omm, R (N x N) the Cholesky factor of S = X^*X (S = R^* R, upper), Rinv = R^-1,
+// T work, Mneg = -S^-1 K; *ok = 0 if S is not positive definite.  All FP64, row-major.
+cudaError_t launch_fp64_check_small(const double2* C, int ldc, int N, double* E, double2* R, double2* Rinv,
+                                    double2* T, double2* Mneg, int* ok, cudaStream_t st);
 
 // ---- k_krylov.cu: batched restarted GMRES over S systems of length n
 struct KrylovDims {

@@ -17,6 +17,7 @@ struct TrsvArgs {
   const long long* node_wb;   // W_b offset (ns x (ns + nb), row-major)
   const int* perm;            // ND -> natural
   const int* bnat;            // boundary natural indices
+  const int* bnd;             // the same boundary unknowns, ND indices
   const int* contrib_ptr;     // n + 1
   const int* contrib_idx;
   long long factor_size;      // complex entries per pole
@@ -53,12 +54,13 @@ struct LeafArgs {
 };
 
 size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb);
-// b (natural, S systems) -> x (natural); ynd, u work buffers.  factor: P poles' blocks.
+// b (ND order, S systems) -> x (natural order); ynd, u, xnd (ND order) work buffers, each
+// S x n except u (urows x S).  factor: P poles' blocks.
 // phases: bit 0 leaves forward, bit 1 levels forward, bit 2 levels backward, bit 3 leaves
 // backward (SPP_ALL = 15); the phases must run in that order.
 constexpr int SPP_LEAF_FWD = 1, SPP_LEVELS_FWD = 2, SPP_LEVELS_BWD = 4, SPP_LEAF_BWD = 8, SPP_ALL = 15;
 cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
-                             const void* b, void* ynd, void* u, void* x, const void* factor, const int* active,
-                             size_t smem, cudaStream_t st);
+                             const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                             const int* active, size_t smem, cudaStream_t st);
 
 }  // namespace omm

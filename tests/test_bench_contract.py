@@ -55,18 +55,21 @@ def fake_library(fail_every=0):
             if fail_every and count["solves"] % fail_every == 0:
                 raise RuntimeError("omm_solve: a CUDA runtime call failed (-6)")
             return dict(iters=20, filters=1, converged=1, energy=-1.0, energy_fp64=-1.0, resid_fp64=0.03,
-                        gmres_iters_max=11, gmres_iters_total=220, gmres_relres_max=1e-5)
+                        gmres_iters_max=11, gmres_iters_total=220, gmres_relres_max=1e-5, grad_norm=1e-3,
+                        resid_orth=1e-3, angle_bound=1e-2)
 
         def energy(self):
             return -1.0
 
         def profile(self, on=True):
-            pass
+            self.mode = on
 
         def profile_read(self):
             names = ("happly", "greenq", "trsv_levels", "orth", "gram", "block_update", "vector", "small",
                      "trsv_leaf")
-            return {k: {"calls": 10, "kernels": 20, "ms": 1.0 + i, "bytes": 1e9} for i, k in enumerate(names)}
+            timed = getattr(self, "mode", False) is True   # per-class events only in profiling mode
+            return {k: {"calls": 10, "kernels": 20, "ms": (1.0 + i) if timed else 0.0, "bytes": 1e9,
+                        "impl_bytes": 2e9} for i, k in enumerate(names)}
 
         def device_bytes(self):
             return 1 << 30
@@ -149,6 +152,11 @@ def test_solve_line_keeps_the_contract(bench, argv, monkeypatch):
     assert rec["e2e"]["h2d_bytes_per_step"] > 0 and rec["gpu_launches"] > 0
     assert rec["roofline"]["bound"] in ("hbm", "alu", "tensor") and rec["roofline"]["frac"] > 0
     assert "workload" in rec["config"] and "l2" in rec["config"]
+    # the per-class profile comes from its own untimed solve, not from the timed region
+    assert rec["kernels"]["pass"].startswith("one untimed solve")
+    assert "counters on, per-class events off" in rec["config"]["timing"]
+    if "accuracy_vs_fp64" in rec:
+        assert "fp64_form_solves_per_s" in rec["accuracy_vs_fp64"] and "accuracy_gates" in rec
 
 
 def test_serve_line_counts_failed_requests(bench, monkeypatch):

@@ -31,17 +31,22 @@ def test_roofline_record_bounds_and_arithmetic():
     """The dominant class's roofline: HBM bytes for the memory-bound classes; for the Gram
     class 48 n N^2 flops per call against FP32 FMA on the CUDA cores (152 SMs x 128 lanes x
     2 x clock) or, on tcgen05, the measured bf16 rate x 1.1 / 2.25."""
+    import types
     import bench
     peaks = {"hbm_gbs": 6655.0, "bf16_tflops": 1937.4, "sm_max_mhz": 2070.0}
-    prof = {"trsv_levels": {"calls": 10, "kernels": 10, "ms": 2.0, "bytes": 1.0e9},
+    prof = {"trsv_levels": {"calls": 10, "kernels": 10, "ms": 2.0, "bytes": 1.0e9, "impl_bytes": 3.0e9},
             "gram": {"calls": 4, "kernels": 8, "ms": 2.0, "bytes": 1.0e8}}
-    r = bench.roofline_record(prof, "trsv_levels", 128, 16384, peaks, 2070.0, 0)
+    wl = types.SimpleNamespace(N=128, n=16384)
+    r = bench.roofline_record(prof, "trsv_levels", wl, peaks, 2070.0, 0, 5)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - 500.0) < 1e-9 and abs(r["frac"] - 500.0 / 6655.0) < 1e-12
-    r = bench.roofline_record(prof, "gram", 128, 16384, peaks, 2000.0, 0)
+    # per call of the class: the algorithmic and the implementation's own bytes
+    assert abs(r["algorithmic_bytes_per_call"] - 1.0e8) < 1e-3
+    assert abs(r["impl_bytes_per_call"] - 3.0e8) < 1e-3
+    r = bench.roofline_record(prof, "gram", wl, peaks, 2000.0, 0, 5)
     flops = 4 * 48.0 * 16384 * 128 ** 2
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - flops / 2.0e-3 / 1e12) < 1e-9
     assert abs(r["peak"] - 152 * 128 * 2 * 2000e6 / 1e12) < 1e-9
-    r = bench.roofline_record(prof, "gram", 128, 16384, peaks, None, 1)
+    r = bench.roofline_record(prof, "gram", wl, peaks, None, 1, 5)
     assert r["bound"] == "tensor" and abs(r["peak"] - 1937.4 * 1.1 / 2.25) < 1e-9

@@ -52,6 +52,26 @@ def test_noalloc_gram_matches_allocating_gram_on_consecutive_calls(omm, prec):
     s.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_gram_with_fewer_splits_matches_allocating_gram(omm, prec):
+    """Shapes whose partials do not fit the array at the allocating Gram's split count: at
+    724 x 724 (n = 16384) the array holds one split where omm_gram uses three; at 256 x 256 it
+    holds eight where omm_gram uses nineteen.  Two calls in a row, each against omm_gram."""
+    m = 128
+    n = m * m
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    s = omm.Solver(2, m, 10.0, np.zeros(n), 8, params=omm.default_params(precision=prec))
+    tol = 1e-13 if prec == 0 else 2e-6
+    for seed, (na, nb) in enumerate([(724, 724), (256, 256)]):
+        A = torch.from_numpy(gaussian_block(n, na, seed=30 + seed)).to(device="cuda", dtype=dt)
+        B = A if seed == 0 else torch.from_numpy(gaussian_block(n, nb, seed=40 + seed)).to(device="cuda", dtype=dt)
+        got = noalloc(omm, prec, A, B, n)
+        ref = s.gram(A, B).cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+        del A, B
+    s.close()
+
+
 def test_noalloc_gram_rejects_sizes_beyond_its_array(omm):
     n = 256
     A = torch.zeros((1024, n), dtype=torch.complex64, device="cuda")

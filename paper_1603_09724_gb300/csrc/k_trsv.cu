@@ -227,6 +227,168 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
 }
 
 
+// Split-K product for the upper tree heights, where one pole's nodes give too few CTAs
+// for the tiled kernel above to keep the SMs busy and each of its threads walks the
+// whole inner dimension K alone.  A CTA of 32 * KS threads computes one RBS x 16 tile
+// (rows x right-hand sides) of one node's product: warp w accumulates the slice
+// [w * kw, (w + 1) * kw) of K over its own copy of the tile (4 rows x TCS columns per
+// lane, W rows staged per warp in WK-wide chunks, the next chunk's loads in flight while
+// the current one is used), and the KS partial tiles are summed in shared memory in a
+// fixed order, so the result does not depend on timing.  Shared memory: the
+// right-hand-side block Bs [K][16] (reused for the partial tiles) and the warp-private W
+// chunks.
+constexpr int SK_RT = 16;   // right-hand sides per CTA
+constexpr int SK_WK = 8;    // k values per staged W chunk
+
+template <typename T, int KS, int RBS>
+size_t sk_smem_bytes(int K) {
+  const size_t cs = sizeof(cx_t<T>);
+  const size_t bs = std::max((size_t)K * SK_RT, (size_t)KS * RBS * (SK_RT + 1));
+  return (bs + (size_t)KS * SK_WK * (RBS + 1)) * cs;
+}
+
+template <typename T, bool FWD, int KS, int RBS>
+__global__ void __launch_bounds__(32 * KS) trsv_gemm_sk_kernel(TrsvArgs a, const int* __restrict__ blocks,
+                                                               cx_t<T>* __restrict__ ynd, cx_t<T>* __restrict__ u,
+                                                               cx_t<T>* __restrict__ x, cx_t<T>* __restrict__ xnd,
+                                                               const cx_t<T>* __restrict__ factor,
+                                                               const int* __restrict__ active, int split) {
+  using C = cx_t<T>;
+  constexpr int NTH = 32 * KS;
+  constexpr int RT = SK_RT;
+  constexpr int TCS = RBS * RT / (32 * 4);   // columns per lane (4 rows per lane)
+  constexpr int CGS = RT / TCS;              // column groups across a warp
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int node = blocks[2 * (blockIdx.y / split)];
+  const int r0 = blocks[2 * (blockIdx.y / split) + 1] + (int)(blockIdx.y % split) * RBS;
+  const int p = blockIdx.z;
+  const int c0 = blockIdx.x * RT;
+  const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
+  const int K = FWD ? ns : ns + nb;
+  const int M = FWD ? ns + nb : ns;
+  if (r0 >= M) return;   // a split past the node's last row (uniform over the CTA)
+  C* Bs = reinterpret_cast<C*>(smem_raw);                                   // [K][RT]
+  const size_t bs_elems = max((size_t)K * RT, (size_t)KS * RBS * (RT + 1));
+  C* Wall = Bs + bs_elems;                                                   // [KS][WK][RBS + 1]
+  const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
+  const int tid = threadIdx.x;
+  // ---- right-hand-side block (i fastest: contiguous runs of one system's column)
+  constexpr int FB = 8;
+  const int boff = a.node_boff[node];
+  for (int base = tid; base < K * RT; base += FB * NTH) {
+    C v[FB];
+#pragma unroll
+    for (int q = 0; q < FB; ++q) {
+      const int idx = base + q * NTH;
+      const int i = idx % K, cc = idx / K;
+      const int c = c0 + cc;
+      v[q] = mk<C>(0, 0);
+      if (idx < K * RT && c < a.N) {
+        const size_t s = (size_t)p * a.N + c;
+        if (FWD) {
+          if (!active || active[s]) v[q] = xnd[s * a.n + off + i];
+        } else {
+          v[q] = (i < ns) ? ynd[s * a.n + off + i] : xnd[s * a.n + a.bnd[boff + i - ns]];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < FB; ++q) {
+      const int idx = base + q * NTH;
+      if (idx < K * RT) Bs[(idx % K) * RT + idx / K] = v[q];
+    }
+  }
+  __syncthreads();
+  // ---- this warp's slice of K
+  const int w = tid >> 5, lane = tid & 31;
+  const int rg = lane / CGS, cg = lane % CGS;
+  const int kw = (K + KS - 1) / KS;
+  const int kb = w * kw, ke = min(K, kb + kw);
+  C* Ws = Wall + (size_t)w * SK_WK * (RBS + 1);
+  C acc[4][TCS];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TCS; ++j) acc[i][j] = mk<C>(0, 0);
+  constexpr int WPL = RBS * SK_WK / 32;   // W values per lane per chunk
+  C wv[WPL];
+  auto load_w = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+      const int idx = lane + 32 * q;
+      const int kk = idx % SK_WK, rr = idx / SK_WK;   // k fastest: runs of one W row
+      const int r = r0 + rr, k = k0 + kk;
+      wv[q] = (r < M && k < ke) ? W[(size_t)r * K + k] : mk<C>(0, 0);
+    }
+  };
+  if (kb < ke) load_w(kb);
+  for (int k0 = kb; k0 < ke; k0 += SK_WK) {
+    __syncwarp();   // the previous chunk has been read
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+      const int idx = lane + 32 * q;
+      Ws[(idx % SK_WK) * (RBS + 1) + idx / SK_WK] = wv[q];
+    }
+    __syncwarp();
+    if (k0 + SK_WK < ke) load_w(k0 + SK_WK);   // next chunk in flight during the products
+    const int kmax = min(SK_WK, ke - k0);
+    for (int kk = 0; kk < kmax; ++kk) {
+      C av[4], bv[TCS];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = Ws[kk * (RBS + 1) + rg * 4 + i];
+#pragma unroll
+      for (int j = 0; j < TCS; ++j) bv[j] = Bs[(k0 + kk) * RT + cg * TCS + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TCS; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+    }
+  }
+  // ---- partial tiles -> Bs region [KS][RBS][RT + 1], summed in warp order into slice 0
+  __syncthreads();   // every warp is done with Bs
+  C* Rp = Bs;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TCS; ++j) Rp[((size_t)w * RBS + rg * 4 + i) * (RT + 1) + cg * TCS + j] = acc[i][j];
+  __syncthreads();
+  for (int o = tid; o < RBS * RT; o += NTH) {
+    const int rr = o / RT, cc = o % RT;
+    C sum = Rp[(size_t)rr * (RT + 1) + cc];
+#pragma unroll
+    for (int ww = 1; ww < KS; ++ww) sum = cadd(sum, Rp[((size_t)ww * RBS + rr) * (RT + 1) + cc]);
+    Rp[(size_t)rr * (RT + 1) + cc] = sum;
+  }
+  __syncthreads();
+  const int rows = min(RBS, M - r0);
+  if (FWD) {
+    const int ny = max(0, min(rows, ns - r0));
+    for (int idx = tid; idx < ny * RT; idx += NTH) {
+      const int rr = idx % ny, cc = idx / ny;
+      const int c = c0 + cc;
+      if (c < a.N) ynd[((size_t)p * a.N + c) * a.n + off + r0 + rr] = Rp[(size_t)rr * (RT + 1) + cc];
+    }
+    const int uoff = a.node_uoff[node];
+    for (int idx = tid; idx < (rows - ny) * RT; idx += NTH) {
+      const int cc = idx % RT, rr = ny + idx / RT;
+      const int c = c0 + cc;
+      if (c < a.N) u[(size_t)(uoff + r0 + rr - ns) * a.S + (size_t)p * a.N + c] = Rp[(size_t)rr * (RT + 1) + cc];
+    }
+  } else {
+    for (int idx = tid; idx < rows * RT; idx += NTH) {
+      const int rr = idx % rows, cc = idx / rows;
+      const int c = c0 + cc;
+      if (c >= a.N) continue;
+      const size_t s = (size_t)p * a.N + c;
+      if (active && !active[s]) continue;
+      const C v = Rp[(size_t)rr * (RT + 1) + cc];
+      xnd[s * a.n + off + r0 + rr] = v;
+      x[s * a.n + a.perm[off + r0 + rr]] = v;
+    }
+  }
+}
+
+
 // ---- leaves: banded substitution with the leaf's own L and U (the fill of a leaf stays
 // inside the band of its x-fastest ordering) and sparse couplings to the halo:
 //   forward:  y = L^-1 b_S,  u_s = F_BS (U^-1 y)       (b_S: a contiguous ND range)
@@ -439,11 +601,57 @@ static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count,
 // Tile choice per level from its largest row count mmax (M = ns + nb forward, ns backward)
 // and its CTA count: 16-row tiles for the thin bottom separators (7 and 15 rows in 2D),
 // 32 x RT/2 tiles where 64 x RT leaves the GPU underfilled, else 64 x RT.
+template <typename T, bool FWD, int KS, int RBS>
+static cudaError_t launch_level_sk(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
+                                   void* ynd, void* u, void* x, void* xnd, const void* factor, const int* active,
+                                   cudaStream_t st) {
+  using C = cx_t<T>;
+  auto k = trsv_gemm_sk_kernel<T, FWD, KS, RBS>;
+  cudaError_t e = raise_smem_limit((const void*)k);
+  if (e != cudaSuccess) return e;
+  const int split = (std::min(RB, mmax) + RBS - 1) / RBS;   // RBS-row CTAs per 64-row host block
+  const dim3 grid((a.N + SK_RT - 1) / SK_RT, count * split, P);
+  k<<<grid, 32 * KS, sk_smem_bytes<T, KS, RBS>(kmax), st>>>(a, blocks, (C*)ynd, (C*)u, (C*)x, (C*)xnd,
+                                                            (const C*)factor, active, split);
+  return cudaGetLastError();
+}
+
+// Split-K launch for a level whose grid is small and whose inner dimension is long:
+// 16-row tiles for nodes of at most 16 rows, else 32; 8 warps per CTA from K = 128, else 4.
+template <typename T, bool FWD>
+static bool try_level_sk(cudaError_t* err, const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax,
+                         int P, void* ynd, void* u, void* x, void* xnd, const void* factor, const int* active,
+                         cudaStream_t st) {
+  if (kmax < 48) return false;
+  const int KS = kmax >= 128 ? 8 : 4;
+  const int RBS = mmax <= 16 ? 16 : 32;
+  const size_t sm = KS == 8 ? (RBS == 16 ? sk_smem_bytes<T, 8, 16>(kmax) : sk_smem_bytes<T, 8, 32>(kmax))
+                            : (RBS == 16 ? sk_smem_bytes<T, 4, 16>(kmax) : sk_smem_bytes<T, 4, 32>(kmax));
+  if (sm > 200 * 1024) return false;
+  if (KS == 8 && RBS == 16)
+    *err = launch_level_sk<T, FWD, 8, 16>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+  else if (KS == 8)
+    *err = launch_level_sk<T, FWD, 8, 32>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+  else if (RBS == 16)
+    *err = launch_level_sk<T, FWD, 4, 16>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+  else
+    *err = launch_level_sk<T, FWD, 4, 32>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+  return true;
+}
+
 template <typename T, bool FWD>
 static cudaError_t run_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
                              const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
                              const int* active, cudaStream_t st) {
   constexpr int RT = TrsvCfg<T>::RT;
+  {
+    // grids that leave most SMs idle with the tiled kernel: split K across warps instead
+    const long tiled = (long)count * ((a.N + RT - 1) / RT) * P * ((std::min(RB, mmax) + 31) / 32);
+    cudaError_t e = cudaSuccess;
+    if (tiled < 4 * 152 && try_level_sk<T, FWD>(&e, a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor,
+                                                 active, st))
+      return e;
+  }
   if (mmax <= 16)
     return launch_level<T, FWD, 16, RT, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
   const long ctas = (long)count * ((a.N + RT - 1) / RT) * P;

@@ -101,6 +101,13 @@ typedef struct {
                            rule).  Several let the latency-bound top of the elimination
                            tree of one group overlap the other groups' work; use 1 when
                            many handles already run concurrently (serving).           */
+  int trsv_persistent;  /* 1: the supernode heights of the triangular solves of all poles
+                           run in one cooperative launch per application (grid barriers
+                           between the phases, every wait bounded); 0 (default): one
+                           launch per height and direction on trsv_streams streams,
+                           which measured faster (the poles' heights overlap instead of
+                           marching in step).  Keep 0 when several handles run at once
+                           on one GPU (serving)                                         */
   int fixed_iters;      /* > 0: every CG round runs exactly this many iterations of
                            Algorithm 1 (no energy test; a fixed launch schedule for
                            timing and capture); 0: the energy criterion and maxit      */
@@ -140,7 +147,7 @@ const char* omm_last_error_message(void);
 
 /* Defaults: FP64, sparsifying inner preconditioner, GMRES(15) x 5 cycles, rtol 1e-5
  * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter,
- * fixed_iters 0, refilter_rtol 0 (= gmres_rtol), gap 0 (no angle bound).
+ * trsv_persistent 0, fixed_iters 0, refilter_rtol 0 (= gmres_rtol), gap 0 (no angle bound).
  * Errors: OMM_EINVAL (p NULL). */
 omm_status omm_default_params(omm_params* p);
 

@@ -35,7 +35,8 @@ class omm_params(C.Structure):
                 ("gmres_rtol", C.c_double), ("gmres_fixed", C.c_int), ("stencil_radius", C.c_int),
                 ("pivot_floor", C.c_double), ("tol", C.c_double), ("maxit", C.c_int), ("refilter", C.c_int),
                 ("gram_tensor", C.c_int), ("real_orbitals", C.c_int), ("trsv_streams", C.c_int),
-                ("fixed_iters", C.c_int), ("refilter_rtol", C.c_double), ("gap", C.c_double)]
+                ("trsv_persistent", C.c_int), ("fixed_iters", C.c_int), ("refilter_rtol", C.c_double),
+                ("gap", C.c_double)]
 
 
 class omm_stats(C.Structure):

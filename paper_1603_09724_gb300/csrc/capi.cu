@@ -191,6 +191,7 @@ struct omm_ctx {
   void* leafvals = nullptr;     // P * leaf_size complex
   int* d_bblocks = nullptr;
   int* d_lunk = nullptr;                    // unknowns of each tree height (ND indices)
+  unsigned* d_trsv_bar = nullptr;           // grid barrier of the persistent level launch: count, generation, error
   // algorithmic complex elements of the triangular-solve phases: per system and per pole
   double tb_leaf_fwd_sys = 0, tb_leaf_bwd_sys = 0, tb_leaf_pole = 0, tb_lvl_sys = 0, tb_lvl_pole = 0;
   double n_leaf = 0, n_sep = 0;   // unknowns in the leaves / in the separators (algorithmic bytes)
@@ -547,7 +548,16 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
     }
   }
   auto spp = [&](int phases) -> omm_status {
-    if (ng == 1)
+    if (phases == (SPP_LEVELS_FWD | SPP_LEVELS_BWD) && h->prm.trsv_persistent) {
+      // every height of every pole in one cooperative launch (falls back to the launches per
+      // height below when the structure does not fit it)
+      bool done = false;
+      OMM_TRY(cuda_status(launch_spp_levels_persistent(h->dbl, a, lv, has_leaves, P, tmp, h->ynd, h->ubuf, Z, h->xnd,
+                                                       h->factor, active, h->d_trsv_bar, h->st, &done),
+                          "spp levels"));
+      if (done) return OMM_OK;
+    }
+    if (ng == 1 || (h->prm.trsv_persistent && phases != (SPP_LEVELS_FWD | SPP_LEVELS_BWD)))
       return cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, P, tmp, h->ynd, h->ubuf, Z, h->xnd, h->factor,
                                           active, h->trsv_smem, h->st),
                          "spp");
@@ -571,7 +581,8 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
     }
     return OMM_OK;
   };
-  const int ns = ng;   // launches per kernel (one per stream)
+  const int ns = h->prm.trsv_persistent ? 1 : ng;   // launches per kernel (one per stream)
+  if (h->prm.trsv_persistent) nk = 1;   // (the fallback per height counts as one too)
   // Algorithmic bytes of the triangular solves (L then U): each unknown's right-hand side
   // read and y written, y read and x written (4 per unknown and active system), and each
   // pole's factor read once (leaf values split over the two leaf passes).  The
@@ -676,14 +687,22 @@ omm_status gmres_stats(omm_ctx* h) {
 
 omm_status read_scalars(omm_ctx* h) {
   OMM_TRY(cuda_status(cudaMemcpyAsync(h->sc_h, h->sc, sizeof(OmmScalars), cudaMemcpyDeviceToHost, h->st), "sc"));
-  if (h->tc_err) {
-    int e = 0;
+  int e = 0;
+  unsigned eb = 0;
+  if (h->tc_err)
     OMM_TRY(cuda_status(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st), "tc err"));
-    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sc sync"));
-    if (e) return OMM_ETIMEOUT;
-    return OMM_OK;
+  if (h->d_trsv_bar)
+    OMM_TRY(cuda_status(cudaMemcpyAsync(&eb, h->d_trsv_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st),
+                        "trsv err"));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sc sync"));
+  if (eb) {
+    // a bounded barrier wait of the persistent triangular solves gave up: clear the
+    // barrier for the next launch and report it
+    omm_internal_set_message("a grid barrier of the triangular solves timed out");
+    OMM_TRY(cuda_status(cudaMemsetAsync(h->d_trsv_bar, 0, 4 * sizeof(unsigned), h->st), "memset"));
+    return OMM_ETIMEOUT;
   }
-  return cuda_status(cudaStreamSynchronize(h->st), "sc sync");
+  return e ? OMM_ETIMEOUT : OMM_OK;
 }
 
 // C = A^H B (complex double out): tensor cores for complex64 when enabled, else CUDA cores
@@ -951,6 +970,8 @@ omm_status build_spp(omm_ctx* h) {
       }
       OMM_TRY(upload_vec(h, &h->d_lunk, lunk));
     }
+    OMM_TRY(h->dalloc_t(&h->d_trsv_bar, 4 * sizeof(unsigned)));
+    OMM_TRY(cuda_status(cudaMemsetAsync(h->d_trsv_bar, 0, 4 * sizeof(unsigned), h->st), "memset"));
     OMM_TRY(upload_vec(h, &h->d_leaf_nodes, s.leaf_nodes));
     OMM_TRY(upload_vec(h, &h->d_leaf_voff, s.leaf_voff));
     OMM_TRY(upload_vec(h, &h->d_leaf_ioff_bs, s.leaf_ioff_bs));
@@ -1002,6 +1023,7 @@ omm_status omm_default_params(omm_params* p) {
   p->real_orbitals = 0;
   p->trsv_streams = 0;
   p->fixed_iters = 0;
+  p->trsv_persistent = 0;
   p->refilter_rtol = 0.0;
   p->gap = 0.0;
   return OMM_OK;
@@ -1044,6 +1066,7 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
   if (p) prm = *p;
   if (prm.gmres_m < 1 || prm.gmres_m > 15 || prm.gmres_cycles < 1 || prm.maxit < 0 || prm.refilter < 0 ||
       (prm.precision != OMM_FP64 && prm.precision != OMM_MIXED) || prm.inner < 0 || prm.inner > 2 ||
+      prm.trsv_persistent < 0 || prm.trsv_persistent > 1 ||
       prm.stencil_radius != 1 || prm.trsv_streams < 0 || prm.trsv_streams > omm_ctx::kTrsvStreams ||
       !(prm.gmres_rtol >= 0.0) || !std::isfinite(prm.gmres_rtol) || !(prm.tol >= 0.0) || !std::isfinite(prm.tol) ||
       !(prm.pivot_floor >= 0.0) || !std::isfinite(prm.pivot_floor) || !std::isfinite(shift) || prm.fixed_iters < 0 ||

@@ -21,6 +21,7 @@
 // staged in shared memory and 4 x (RT/8) outputs per thread.  Leaves (height 0) use
 // their banded LU instead of dense W blocks (leaf_kernel).
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "trsv.h"
@@ -44,15 +45,16 @@ constexpr int KT = 16;   // k step of the product
 // on a chain of loads, so the grid needs many CTAs.
 constexpr int AS_I = 8;
 
+// Update rows, ynd and xnd are read with ld.global.cg (L2, not the SM's L1): inside the
+// persistent launch below, other SMs wrote them earlier in the same kernel.
 template <typename T>
-__global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
-                                                              size_t nsys, const cx_t<T>* __restrict__ b,
-                                                              const cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
-                                                              const int* __restrict__ active) {
+__device__ __forceinline__ void assemble_tile(const TrsvArgs& a, const int* __restrict__ lunk, int cnt, size_t nsys,
+                                              const cx_t<T>* __restrict__ b, const cx_t<T>* u, cx_t<T>* x,
+                                              const int* __restrict__ active, int bx, int by) {
   using C = cx_t<T>;
   __shared__ C tile[AS_I][33];
-  const int i0 = blockIdx.x * AS_I;
-  const size_t s0 = (size_t)blockIdx.y * 32;
+  const int i0 = bx * AS_I;
+  const size_t s0 = (size_t)by * 32;
   const int t = threadIdx.x;
   {
     const int ii = t % AS_I, ss = t / AS_I;   // unknown fastest
@@ -71,13 +73,13 @@ __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const i
       C acc = tile[ii][ss];
       int e = e0;
       for (; e + 4 <= e1; e += 4) {   // four independent loads in flight, subtracted in order
-        const C v0 = u[(size_t)a.contrib_idx[e] * a.S + s];
-        const C v1 = u[(size_t)a.contrib_idx[e + 1] * a.S + s];
-        const C v2 = u[(size_t)a.contrib_idx[e + 2] * a.S + s];
-        const C v3 = u[(size_t)a.contrib_idx[e + 3] * a.S + s];
+        const C v0 = __ldcg(u + (size_t)a.contrib_idx[e] * a.S + s);
+        const C v1 = __ldcg(u + (size_t)a.contrib_idx[e + 1] * a.S + s);
+        const C v2 = __ldcg(u + (size_t)a.contrib_idx[e + 2] * a.S + s);
+        const C v3 = __ldcg(u + (size_t)a.contrib_idx[e + 3] * a.S + s);
         acc = csub(csub(csub(csub(acc, v0), v1), v2), v3);
       }
-      for (; e < e1; ++e) acc = csub(acc, u[(size_t)a.contrib_idx[e] * a.S + s]);
+      for (; e < e1; ++e) acc = csub(acc, __ldcg(u + (size_t)a.contrib_idx[e] * a.S + s));
       tile[ii][ss] = acc;
     }
   }
@@ -90,37 +92,40 @@ __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const i
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
+                                                              size_t nsys, const cx_t<T>* __restrict__ b,
+                                                              const cx_t<T>* u, cx_t<T>* x, const int* __restrict__ active) {
+  assemble_tile<T>(a, lunk, cnt, nsys, b, u, x, active, blockIdx.x, blockIdx.y);
+}
+
 // Grid: (right-hand-side tiles, row blocks, poles).  The tiles of one row block are
 // adjacent in launch order, so the W rows they share are read from DRAM once.
 // RBV rows x RTV right-hand sides per CTA with NTH threads, 4 rows x TC columns per thread.
 // The host's row blocks are 64 rows; a smaller RBV splits each into `split` CTAs (grid.y):
 // for the top of the tree, where 64-row blocks leave most SMs idle, and for thin nodes.
 template <typename T, bool FWD, int RBV, int RTV, int NTH>
-__global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks,
-                                                               const cx_t<T>* __restrict__ b, cx_t<T>* __restrict__ ynd,
-                                                               cx_t<T>* __restrict__ u, cx_t<T>* __restrict__ x,
-                                                               cx_t<T>* __restrict__ xnd,
-                                                               const cx_t<T>* __restrict__ factor,
-                                                               const int* __restrict__ active, int split) {
+__device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restrict__ blocks, cx_t<T>* ynd, cx_t<T>* u,
+                                          cx_t<T>* x, cx_t<T>* xnd, const cx_t<T>* __restrict__ factor,
+                                          const int* __restrict__ active, int split, int bx, int by, int bz,
+                                          unsigned char* smem_raw) {
   using C = cx_t<T>;
   constexpr int RT = RTV;
   constexpr int TC = RTV * (RBV / 4) / NTH;   // columns per thread
   constexpr int CG = RTV / TC;                // column groups
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Bs = reinterpret_cast<C*>(smem_raw);   // [K][RT]
   __shared__ C As[2][KT][RBV + 1];                 // double-buffered W tiles
   C(*Cs)[RT + 1] = reinterpret_cast<C(*)[RT + 1]>(smem_raw);   // output staging, reuses Bs after the product
-  const int node = blocks[2 * (blockIdx.y / split)];
-  const int r0 = blocks[2 * (blockIdx.y / split) + 1] + (int)(blockIdx.y % split) * RBV;
-  const int p = blockIdx.z;
-  const int c0 = blockIdx.x * RT;
+  const int node = blocks[2 * (by / split)];
+  const int r0 = blocks[2 * (by / split) + 1] + (by % split) * RBV;
+  const int p = bz;
+  const int c0 = bx * RT;
   const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
   const int K = FWD ? ns : ns + nb;
   const int M = FWD ? ns + nb : ns;
   if (r0 >= M) return;   // a split past the node's last row (uniform over the CTA)
   const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
-  (void)b;
   // ---- right-hand-side block, i fastest (contiguous runs of one system's column); FB
   // independent loads in flight per thread
   constexpr int FB = 8;
@@ -136,9 +141,9 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
       if (idx < K * RT && c < a.N) {
         const size_t s = (size_t)p * a.N + c;
         if (FWD) {   // assembled by assemble_kernel into xnd
-          if (!active || active[s]) v[q] = xnd[s * a.n + off + i];
+          if (!active || active[s]) v[q] = __ldcg(xnd + s * a.n + off + i);
         } else {     // y_S, then x_B from the ancestors' solutions (runs in ND order)
-          v[q] = (i < ns) ? ynd[s * a.n + off + i] : xnd[s * a.n + a.bnd[boff + i - ns]];
+          v[q] = __ldcg((i < ns) ? ynd + s * a.n + off + i : xnd + s * a.n + a.bnd[boff + i - ns]);
         }
       }
     }
@@ -226,6 +231,16 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
   }
 }
 
+template <typename T, bool FWD, int RBV, int RTV, int NTH>
+__global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* __restrict__ blocks, cx_t<T>* ynd,
+                                                        cx_t<T>* u, cx_t<T>* x, cx_t<T>* xnd,
+                                                        const cx_t<T>* __restrict__ factor,
+                                                        const int* __restrict__ active, int split) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  gemm_tile<T, FWD, RBV, RTV, NTH>(a, blocks, ynd, u, x, xnd, factor, active, split, blockIdx.x, blockIdx.y,
+                                   blockIdx.z, smem_raw);
+}
+
 
 // Split-K product for the upper tree heights, where one pole's nodes give too few CTAs
 // for the tiled kernel above to keep the SMs busy and each of its threads walks the
@@ -248,21 +263,19 @@ size_t sk_smem_bytes(int K) {
 }
 
 template <typename T, bool FWD, int KS, int RBS>
-__global__ void __launch_bounds__(32 * KS) trsv_gemm_sk_kernel(TrsvArgs a, const int* __restrict__ blocks,
-                                                               cx_t<T>* __restrict__ ynd, cx_t<T>* __restrict__ u,
-                                                               cx_t<T>* __restrict__ x, cx_t<T>* __restrict__ xnd,
-                                                               const cx_t<T>* __restrict__ factor,
-                                                               const int* __restrict__ active, int split) {
+__device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __restrict__ blocks, cx_t<T>* ynd,
+                                             cx_t<T>* u, cx_t<T>* x, cx_t<T>* xnd, const cx_t<T>* __restrict__ factor,
+                                             const int* __restrict__ active, int split, int bx, int by, int bz,
+                                             unsigned char* smem_raw) {
   using C = cx_t<T>;
   constexpr int NTH = 32 * KS;
   constexpr int RT = SK_RT;
   constexpr int TCS = RBS * RT / (32 * 4);   // columns per lane (4 rows per lane)
   constexpr int CGS = RT / TCS;              // column groups across a warp
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int node = blocks[2 * (blockIdx.y / split)];
-  const int r0 = blocks[2 * (blockIdx.y / split) + 1] + (int)(blockIdx.y % split) * RBS;
-  const int p = blockIdx.z;
-  const int c0 = blockIdx.x * RT;
+  const int node = blocks[2 * (by / split)];
+  const int r0 = blocks[2 * (by / split) + 1] + (by % split) * RBS;
+  const int p = bz;
+  const int c0 = bx * RT;
   const int ns = a.node_ns[node], nb = a.node_nb[node], off = a.node_off[node];
   const int K = FWD ? ns : ns + nb;
   const int M = FWD ? ns + nb : ns;
@@ -286,9 +299,9 @@ __global__ void __launch_bounds__(32 * KS) trsv_gemm_sk_kernel(TrsvArgs a, const
       if (idx < K * RT && c < a.N) {
         const size_t s = (size_t)p * a.N + c;
         if (FWD) {
-          if (!active || active[s]) v[q] = xnd[s * a.n + off + i];
+          if (!active || active[s]) v[q] = __ldcg(xnd + s * a.n + off + i);
         } else {
-          v[q] = (i < ns) ? ynd[s * a.n + off + i] : xnd[s * a.n + a.bnd[boff + i - ns]];
+          v[q] = __ldcg((i < ns) ? ynd + s * a.n + off + i : xnd + s * a.n + a.bnd[boff + i - ns]);
         }
       }
     }
@@ -386,6 +399,16 @@ __global__ void __launch_bounds__(32 * KS) trsv_gemm_sk_kernel(TrsvArgs a, const
       x[s * a.n + a.perm[off + r0 + rr]] = v;
     }
   }
+}
+
+template <typename T, bool FWD, int KS, int RBS>
+__global__ void __launch_bounds__(32 * KS) trsv_gemm_sk_kernel(TrsvArgs a, const int* __restrict__ blocks,
+                                                               cx_t<T>* ynd, cx_t<T>* u, cx_t<T>* x, cx_t<T>* xnd,
+                                                               const cx_t<T>* __restrict__ factor,
+                                                               const int* __restrict__ active, int split) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  gemm_sk_tile<T, FWD, KS, RBS>(a, blocks, ynd, u, x, xnd, factor, active, split, blockIdx.x, blockIdx.y, blockIdx.z,
+                                smem_raw);
 }
 
 
@@ -594,7 +617,8 @@ static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count,
   const int split = (std::min(RB, mmax) + RBV - 1) / RBV;
   const dim3 grid((a.N + RTV - 1) / RTV, count * split, P);
   const size_t sm = std::max((size_t)kmax * RTV, (size_t)RBV * (RTV + 1)) * sizeof(C);
-  k<<<grid, NTH, sm, st>>>(a, blocks, (const C*)b, (C*)ynd, (C*)u, (C*)x, (C*)xnd, (const C*)factor, active, split);
+  (void)b;
+  k<<<grid, NTH, sm, st>>>(a, blocks, (C*)ynd, (C*)u, (C*)x, (C*)xnd, (const C*)factor, active, split);
   return cudaGetLastError();
 }
 
@@ -699,6 +723,219 @@ static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, co
   if (leaves && (phases & SPP_LEAF_BWD))
     leaf_b<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)xnd, active);
   return cudaGetLastError();
+}
+
+// ---- all supernode heights of one application in one cooperative launch
+// The forward sweep (per height: assembly, then the product) and the backward sweep are a
+// fixed sequence of phases; each phase is a grid of tiles (the same tiles the separate
+// launches above use, for all poles of the launch at once), and a grid-wide barrier
+// separates consecutive phases.  Every CTA of the cooperative launch is resident, so the
+// barrier completes; its waits are still bounded (2 s by %globaltimer): on timeout, or
+// when another CTA already gave up, the kernel sets err and returns.
+enum TrsvPhaseType : int { PH_ASM = 0, PH_FWD_TILE, PH_FWD_SK16, PH_FWD_SK32, PH_BWD_TILE, PH_BWD_SK16, PH_BWD_SK32 };
+
+struct TrsvPhase {
+  int type;
+  int dimx, dimy, dimz;   // tile grid (x fastest)
+  int split;              // CTAs per 64-row host block (products)
+  int off;                // into lunk (assembly) or the (node, row) pairs of the height (products)
+  int cnt;                // unknowns of the height (assembly)
+  int pad;
+};
+constexpr int kMaxPhases = 64;
+struct TrsvPhaseList {
+  int n;
+  TrsvPhase ph[kMaxPhases];
+};
+constexpr int PT = 256;   // threads of the persistent CTA (8 warps)
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bar[0] counts arrivals, bar[1] is the generation; bar[2] is the error flag.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* ok_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    volatile unsigned* verr = bar + 2;
+    bool ok = *verr == 0u;
+    if (ok) {
+      const unsigned g = *gen;
+      __threadfence();
+      if (atomicAdd(bar, 1u) + 1u == nblocks) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        const unsigned long long t0 = global_timer_ns();
+        while (*gen == g) {
+          if (*verr != 0u || global_timer_ns() - t0 > 2000000000ull) {
+            ok = false;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __threadfence();
+    }
+    if (!ok) atomicExch(bar + 2, 1u);
+    *ok_sh = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return *ok_sh != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PT, 2) trsv_levels_kernel(TrsvArgs a, TrsvPhaseList L, const int* __restrict__ fblocks,
+                                                        const int* __restrict__ bblocks, const int* __restrict__ lunk,
+                                                        size_t nsys, const cx_t<T>* __restrict__ b, cx_t<T>* ynd,
+                                                        cx_t<T>* u, cx_t<T>* x, cx_t<T>* xnd,
+                                                        const cx_t<T>* __restrict__ factor,
+                                                        const int* __restrict__ active, unsigned* bar) {
+  constexpr int RT = TrsvCfg<T>::RT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int ok_sh;
+  for (int q = 0; q < L.n; ++q) {
+    const TrsvPhase d = L.ph[q];
+    const int ntasks = d.dimx * d.dimy * d.dimz;
+    for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+      const int bx = t % d.dimx, by = (t / d.dimx) % d.dimy, bz = t / (d.dimx * d.dimy);
+      switch (d.type) {
+        case PH_ASM: assemble_tile<T>(a, lunk + d.off, d.cnt, nsys, b, u, xnd, active, bx, by); break;
+        case PH_FWD_TILE:
+          gemm_tile<T, true, 64, RT, PT>(a, fblocks + d.off, ynd, u, x, xnd, factor, active, d.split, bx, by, bz,
+                                         smem_raw);
+          break;
+        case PH_FWD_SK16:
+          gemm_sk_tile<T, true, 8, 16>(a, fblocks + d.off, ynd, u, x, xnd, factor, active, d.split, bx, by, bz,
+                                       smem_raw);
+          break;
+        case PH_FWD_SK32:
+          gemm_sk_tile<T, true, 8, 32>(a, fblocks + d.off, ynd, u, x, xnd, factor, active, d.split, bx, by, bz,
+                                       smem_raw);
+          break;
+        case PH_BWD_TILE:
+          gemm_tile<T, false, 64, RT, PT>(a, bblocks + d.off, ynd, u, x, xnd, factor, active, d.split, bx, by, bz,
+                                          smem_raw);
+          break;
+        case PH_BWD_SK16:
+          gemm_sk_tile<T, false, 8, 16>(a, bblocks + d.off, ynd, u, x, xnd, factor, active, d.split, bx, by, bz,
+                                        smem_raw);
+          break;
+        default:
+          gemm_sk_tile<T, false, 8, 32>(a, bblocks + d.off, ynd, u, x, xnd, factor, active, d.split, bx, by, bz,
+                                        smem_raw);
+          break;
+      }
+      __syncthreads();   // shared memory is reused by the next tile
+    }
+    if (q + 1 < L.n && !grid_barrier(bar, gridDim.x, &ok_sh)) return;
+  }
+}
+
+// Phase list and dynamic shared memory of the persistent launch; false if a phase does not
+// fit (more phases than kMaxPhases, or tiles beyond 200 KB of shared memory).
+template <typename T>
+static bool build_phases(const TrsvArgs& a, const TrsvLevels& lv, bool leaves, int P, TrsvPhaseList& L, size_t& dyn) {
+  constexpr int RT = TrsvCfg<T>::RT;
+  const size_t cs = sizeof(cx_t<T>);
+  const size_t nsys = (size_t)P * a.N;
+  L.n = 0;
+  dyn = 0;
+  auto push = [&](TrsvPhase p) {
+    if (L.n >= kMaxPhases) return false;
+    L.ph[L.n++] = p;
+    return true;
+  };
+  auto product = [&](bool fwd, int h) {
+    const int kmax = fwd ? lv.fkmax[h] : lv.bkmax[h];
+    const int mmax = fwd ? lv.bkmax[h] : lv.fkmax[h];
+    TrsvPhase p{};
+    p.off = 2 * (fwd ? lv.fstart[h] : lv.bstart[h]);
+    const int count = fwd ? lv.fcount[h] : lv.bcount[h];
+    if (kmax >= 48) {
+      const int RBS = mmax <= 16 ? 16 : 32;
+      p.type = fwd ? (RBS == 16 ? PH_FWD_SK16 : PH_FWD_SK32) : (RBS == 16 ? PH_BWD_SK16 : PH_BWD_SK32);
+      p.split = (std::min(RB, mmax) + RBS - 1) / RBS;
+      p.dimx = (a.N + SK_RT - 1) / SK_RT;
+      dyn = std::max(dyn, RBS == 16 ? sk_smem_bytes<T, 8, 16>(kmax) : sk_smem_bytes<T, 8, 32>(kmax));
+    } else {
+      p.type = fwd ? PH_FWD_TILE : PH_BWD_TILE;
+      p.split = 1;
+      p.dimx = (a.N + RT - 1) / RT;
+      dyn = std::max(dyn, std::max((size_t)kmax * RT, (size_t)RB * (RT + 1)) * cs);
+    }
+    p.dimy = count * p.split;
+    p.dimz = P;
+    return push(p);
+  };
+  const int h0 = leaves ? 1 : 0;
+  for (int h = h0; h < lv.nlevels; ++h) {
+    if (lv.fcount[h] == 0) continue;
+    if (lv.ucount[h] > 0) {
+      TrsvPhase p{};
+      p.type = PH_ASM;
+      p.dimx = (lv.ucount[h] + AS_I - 1) / AS_I;
+      p.dimy = (int)((nsys + 31) / 32);
+      p.dimz = 1;
+      p.off = lv.ustart[h];
+      p.cnt = lv.ucount[h];
+      if (!push(p)) return false;
+    }
+    if (!product(true, h)) return false;
+  }
+  for (int h = lv.nlevels - 1; h >= h0; --h) {
+    if (lv.bcount[h] == 0) continue;
+    if (!product(false, h)) return false;
+  }
+  return L.n > 0 && dyn <= 200 * 1024;
+}
+
+template <typename T>
+static cudaError_t run_levels_persistent(const TrsvArgs& a, const TrsvLevels& lv, bool leaves, int P, const void* b,
+                                         void* ynd, void* u, void* x, void* xnd, const void* factor,
+                                         const int* active, unsigned* bar, cudaStream_t st, bool* done) {
+  using C = cx_t<T>;
+  *done = false;
+  static TrsvPhaseList L;   // host staging of the kernel argument (copied at launch)
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t dyn = 0;
+  if (!build_phases<T>(a, lv, leaves, P, L, dyn)) return cudaSuccess;
+  auto k = trsv_levels_kernel<T>;
+  cudaError_t e = raise_smem_limit((const void*)k);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PT, dyn)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaSuccess;
+  const dim3 grid((unsigned)(per_sm * sms));
+  const size_t nsys = (size_t)P * a.N;
+  const int* fb = lv.fblocks;
+  const int* bb = lv.bblocks;
+  const int* lu = lv.lunk;
+  const C* bp = (const C*)b;
+  C* yp = (C*)ynd;
+  C* up = (C*)u;
+  C* xp = (C*)x;
+  C* xn = (C*)xnd;
+  const C* fp = (const C*)factor;
+  TrsvArgs aa = a;
+  void* args[] = {&aa, &L, &fb, &bb, &lu, (void*)&nsys, &bp, &yp, &up, &xp, &xn, &fp, (void*)&active, &bar};
+  e = cudaLaunchCooperativeKernel((const void*)k, grid, dim3(PT), args, dyn, st);
+  if (e == cudaSuccess) *done = true;
+  return e;
+}
+
+cudaError_t launch_spp_levels_persistent(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, bool leaves, int P,
+                                         const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                                         const int* active, unsigned* bar, cudaStream_t st, bool* done) {
+  if (dbl) return run_levels_persistent<double>(a, lv, leaves, P, b, ynd, u, x, xnd, factor, active, bar, st, done);
+  return run_levels_persistent<float>(a, lv, leaves, P, b, ynd, u, x, xnd, factor, active, bar, st, done);
 }
 
 cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,

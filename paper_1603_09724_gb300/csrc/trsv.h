@@ -63,4 +63,13 @@ cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const Trsv
                              const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
                              const int* active, size_t smem, cudaStream_t st);
 
+// All supernode heights (leaves excluded when `leaves`) of one application, every pole of
+// the launch, in one cooperative launch with grid barriers between the phases; bar: 3
+// unsigned on the device (arrival count, generation, error flag: set when a bounded
+// barrier wait gave up), zero before the first launch.  *done is false when the
+// structure does not fit the persistent kernel (the caller then launches per height).
+cudaError_t launch_spp_levels_persistent(bool dbl, const TrsvArgs& a, const TrsvLevels& lv, bool leaves, int P,
+                                         const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
+                                         const int* active, unsigned* bar, cudaStream_t st, bool* done);
+
 }  // namespace omm

@@ -106,7 +106,7 @@ class OmmServer:
         self.budget = int(hbm_budget)
         self.slots = slots
         # one triangular-solve stream per handle: the server already overlaps handles
-        self.params = dict(precision=backend.OMM_MIXED, maxit=40, tol=1e-10, trsv_streams=1)
+        self.params = dict(precision=backend.OMM_MIXED, maxit=40, tol=1e-10, trsv_streams=1, trsv_persistent=0)
         self.params.update(params)
         self.resident: dict[str, _Resident] = {}
         self.shape_bytes: dict[tuple, int] = {}

@@ -8,8 +8,9 @@
 // Split: x = hi + lo with hi = x rounded to TF32 (19 leading bits) and lo = x - hi;
 // A^T B ~ Ahi^T Bhi + Ahi^T Blo + Alo^T Bhi (the dropped lo*lo term is ~2^-22 relative).
 // Operands are staged by the CTA's threads into shared memory in the no-swizzle K-major
-// core-matrix layout (8 rows x 16 bytes per core matrix); one elected thread issues the
-// MMAs into a 128 x 256 FP32 accumulator in tensor memory; tcgen05.commit signals an
+// core-matrix layout (8 rows x 16 bytes per core matrix), in two stages so that staging
+// overlaps the MMAs of the previous chunk; one elected thread issues the MMAs into a
+// 128 x 256 FP32 accumulator in tensor memory; tcgen05.commit signals the stage's
 // mbarrier; the epilogue reads the accumulator with tcgen05.ld and writes FP32 split-K
 // partials, summed in FP64 in a fixed order by a second kernel.  Every mbarrier wait is
 // bounded: on timeout the kernel records an error code and stops issuing work.
@@ -26,13 +27,14 @@ constexpr int TM = 128;        // rows of C per CTA (columns of A)
 constexpr int TNB = 128;       // columns of B per CTA (-> 256 accumulator columns: Re | Im)
 constexpr int TN = 2 * TNB;
 constexpr int KF = 32;         // floats of K per stage (16 complex)
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;       // 8 warps stage operands; warps 0..3 read the accumulator
 constexpr uint32_t TMEM_COLS = 256;
 
 // bytes per operand tile (KF floats per row, 4 bytes)
 constexpr int A_BYTES = TM * KF * 4;    // 16 KB
 constexpr int B_BYTES = TN * KF * 4;    // 32 KB
-constexpr int SMEM_BYTES = 2 * A_BYTES + 2 * B_BYTES + 1024;   // hi/lo tiles + alignment slack
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // hi / lo tiles of one chunk
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;          // two stages + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -108,18 +110,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }  // namespace
 
 // part: [splits][na][2 * nb] floats (Re block then Im block per row of C)
+// Two operand stages: while the tensor core consumes the hi / lo tiles of chunk c, the
+// CTA's threads stage chunk c + 1 into the other buffers; a buffer is overwritten only
+// after the mbarrier of its previous use (the tcgen05.commit of chunk c - 2) completed.
 __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(const float* __restrict__ A, int na,
                                                              const float* __restrict__ B, int nb, size_t n,
                                                              size_t kchunk, float* __restrict__ part,
                                                              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned operand region
+  // 1024-byte aligned operand region: stage b at base + b * STAGE_BYTES
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sAh = base;
-  unsigned char* sAl = sAh + A_BYTES;
-  unsigned char* sBh = sAl + A_BYTES;
-  unsigned char* sBl = sBh + B_BYTES;
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(const float* __rest
   const size_t ke = (kb + kchunk < n) ? kb + kchunk : n;
 
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -146,28 +148,70 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(const float* __rest
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
 
-  uint32_t phase = 0;
-  bool first = true;
-  const size_t ldf = 2 * n;   // floats per column
-  for (size_t k0 = kb; k0 < ke; k0 += KF / 2) {
-    // ---- stage A (TM columns x KF floats) and B (TNB columns -> B and B~) as hi / lo
-    // thread t handles float pairs: 16 pairs per column row; consecutive threads take
-    // consecutive pairs of one column (coalesced 128-byte column segments)
-    for (int e = tid; e < TM * (KF / 2); e += THREADS) {
+  uint32_t phase[2] = {0u, 0u};   // parity of the next completion of each stage's mbarrier
+  int pending[2] = {0, 0};        // a commit of the stage not yet waited for
+  const size_t ldf = 2 * n;       // floats per column
+  // per thread: EA float pairs of A and EB of B per chunk, loaded one chunk ahead into
+  // registers (all independent loads in flight at once), split and stored when the stage
+  // is free
+  constexpr int EA = TM * (KF / 2) / THREADS, EB = TNB * (KF / 2) / THREADS;
+  float2 va[EA], vb[EB];
+  auto load_chunk = [&](size_t k0) {
+#pragma unroll
+    for (int q = 0; q < EA; ++q) {
+      const int e = tid + q * THREADS;
       const int r = e / (KF / 2), pr = e % (KF / 2);
       const size_t kc = k0 + pr;   // complex index
-      float2 v = make_float2(0.f, 0.f);
-      if (i0 + r < na && kc < ke) v = *reinterpret_cast<const float2*>(A + (size_t)(i0 + r) * ldf + 2 * kc);
+      va[q] = (i0 + r < na && kc < ke) ? *reinterpret_cast<const float2*>(A + (size_t)(i0 + r) * ldf + 2 * kc)
+                                       : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < EB; ++q) {
+      const int e = tid + q * THREADS;
+      const int r = e / (KF / 2), pr = e % (KF / 2);
+      const size_t kc = k0 + pr;
+      vb[q] = (j0 + r < nb && kc < ke) ? *reinterpret_cast<const float2*>(B + (size_t)(j0 + r) * ldf + 2 * kc)
+                                       : make_float2(0.f, 0.f);
+    }
+  };
+  if (kb < ke) load_chunk(kb);
+  int c = 0;
+  for (size_t k0 = kb; k0 < ke; k0 += KF / 2, ++c) {
+    const int sb = c & 1;
+    unsigned char* sAh = base + sb * STAGE_BYTES;
+    unsigned char* sAl = sAh + A_BYTES;
+    unsigned char* sBh = sAl + A_BYTES;
+    unsigned char* sBl = sBh + B_BYTES;
+    if (pending[sb]) {   // the MMAs of chunk c - 2 must be done with this stage
+      if (mbar_wait(&bar[sb], phase[sb])) {
+        phase[sb] ^= 1u;
+        pending[sb] = 0;
+      } else {           // stays pending: the drain below waits once more before dealloc
+        if (tid == 0) atomicExch(err, 1);
+        abort_sh = 1;
+      }
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (abort_sh) break;
+    }
+    // ---- split this chunk (A: TM columns x KF floats; B: TNB columns -> B and B~) into
+    // hi / lo tiles of the free stage
+#pragma unroll
+    for (int q = 0; q < EA; ++q) {
+      const int e = tid + q * THREADS;
+      const int r = e / (KF / 2), pr = e % (KF / 2);
+      const float2 v = va[q];
       const float hx = tf32_hi(v.x), hy = tf32_hi(v.y);
       const uint32_t o = tile_off(r, 2 * pr);
       *reinterpret_cast<float2*>(sAh + o) = make_float2(hx, hy);
       *reinterpret_cast<float2*>(sAl + o) = make_float2(v.x - hx, v.y - hy);
     }
-    for (int e = tid; e < TNB * (KF / 2); e += THREADS) {
+#pragma unroll
+    for (int q = 0; q < EB; ++q) {
+      const int e = tid + q * THREADS;
       const int r = e / (KF / 2), pr = e % (KF / 2);
-      const size_t kc = k0 + pr;
-      float2 v = make_float2(0.f, 0.f);
-      if (j0 + r < nb && kc < ke) v = *reinterpret_cast<const float2*>(B + (size_t)(j0 + r) * ldf + 2 * kc);
+      const float2 v = vb[q];
       const float hx = tf32_hi(v.x), hy = tf32_hi(v.y);
       const uint32_t o = tile_off(r, 2 * pr);
       const uint32_t ot = tile_off(TNB + r, 2 * pr);
@@ -177,37 +221,40 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(const float* __rest
       *reinterpret_cast<float2*>(sBh + ot) = make_float2(hy, -hx);
       *reinterpret_cast<float2*>(sBl + ot) = make_float2(v.y - hy, -(v.x - hx));
     }
+    // the next chunk's loads are in flight while this chunk is issued and consumed
+    if (k0 + KF / 2 < ke) load_chunk(k0 + KF / 2);
     // make the generic-proxy shared stores visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0 && !abort_sh) {
+    if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
 #pragma unroll
       for (int s = 0; s < KF / 8; ++s) {   // K = 8 tf32 per MMA = 2 core matrices = 256 bytes
         const uint32_t off = s * 256;
-        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), first ? 0u : 1u);
-        first = false;
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), (c == 0 && s == 0) ? 0u : 1u);
         mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), 1u);
         mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);
       }
-      mma_commit(&bar);
+      mma_commit(&bar[sb]);
     }
-    // all threads wait until the MMAs have consumed the tiles before overwriting them
-    if (!mbar_wait(&bar, phase)) {
-      if (tid == 0) atomicExch(err, 1);   // 1: an MMA batch did not complete in time
+    pending[sb] = 1;
+  }
+  // ---- the last (one or two) commits, and after a timeout the batch that did not
+  // finish in time (bounded again), before the accumulator is read or freed
+  for (int sb = 0; sb < 2; ++sb) {
+    if (!pending[sb]) continue;
+    if (!mbar_wait(&bar[sb], phase[sb])) {
+      if (tid == 0) atomicExch(err, 1);
       abort_sh = 1;
     }
-    __syncwarp();
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (abort_sh) break;
   }
-  // ---- epilogue: TMEM lane = row of C, column = [Re | Im] index.  The condition must be
-  // uniform across the CTA (tcgen05.ld is .sync.aligned): `first` is cleared by the
-  // issuing thread only, so the test uses the K range every thread sees.
-  if (!abort_sh && kb < ke) {
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  // ---- epilogue (warps 0..3: TMEM lanes 32 w .. 32 w + 31 = rows of C; column = [Re | Im]
+  // index).  The condition is uniform across each warp (tcgen05.ld is .sync.aligned).
+  if (!abort_sh && kb < ke && warp < 4) {
     const int row = warp * 32 + lane;
     float* out = part + ((size_t)blockIdx.z * na + (i0 + row)) * (2 * (size_t)nb);
     for (int c0 = 0; c0 < TN; c0 += 16) {
@@ -229,7 +276,6 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(const float* __rest
       }
     }
   }
-  if (abort_sh) mbar_wait(&bar, phase ^ 1);   // bounded: let any MMA still in flight finish
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   __syncwarp();

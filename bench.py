@@ -37,7 +37,8 @@ def args_parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="smooth2d-128",
                     help="smooth2d-128 (the default line), wells2d-32, lattice3d-48")
-    ap.add_argument("--gram-tensor", type=int, default=0, help="1: Grams on the tcgen05 tensor cores (TF32 x 3)")
+    ap.add_argument("--gram-tensor", type=int, default=1,
+                    help="1: complex64 Grams on the tcgen05 tensor cores (TF32 x 3); 0: FP32 CUDA cores")
     ap.add_argument("--precond", default="pole", choices=["pole", "projector", "gtpa"],
                     help="pole: the pole expansion every iteration (Sec. 3.1); projector: U U^* precomputed by "
                          "Algorithm 2 inside each timed solve (Sec. 3.3); gtpa: the Fourier-diagonal TPA-type "
@@ -61,11 +62,14 @@ def args_parse():
                     help="GMRES tolerance of the refilter rounds (0: --rtol)")
     ap.add_argument("--N", type=int, default=0, help="override N (reduced case for profiler captures only)")
     ap.add_argument("--P", type=int, default=0, help="override P (reduced case for profiler captures only)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "graph"],
                     help="solve: the default line; batch: 64 uneven Hamiltonians at once; serve: Poisson arrivals")
     ap.add_argument("--requests", type=int, default=120, help="serve mode: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="batch/serve: concurrent solves")
+    ap.add_argument("--mix", default="2d", choices=["2d", "full"],
+                    help="serve: '2d' the twelve 2D well Hamiltonians; 'full' adds four 2D ones with N in "
+                         "[129, 256] and the 3D lattice on 32^3 (N = 64) and 48^3 (N = 64, 256)")
     ap.add_argument("--orbitals", default="real", choices=["real", "complex"],
                     help="real: real X (eq. lst writes Y real), conjugate pole pairs folded (P/2 solves); complex: P solves")
     return ap.parse_args()
@@ -484,9 +488,14 @@ def run_ours(a):
 
 # DRAM bytes one call of a kernel class moved in an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum summed over the class's kernels for one call, scaled to the bench
-# workload's systems), keyed by class; a class is absent until captured for its current
-# kernels.
-TRAFFIC_PER_CALL = {}
+# workload's systems), keyed by (workload, N, class); absent until captured for the class's
+# current kernels.
+TRAFFIC_PER_CALL = {
+    # profiles/traffic_trsv_smooth2d-128_N64.md: 197.7 MB read per call at N = 64 (S = 512),
+    # the vector part scaled to S = 1024, the factor part (71.0 MB) as measured; writes stay
+    # in L2 and are not attributed to these kernels
+    ("smooth2d-128", 128, "trsv_levels"): 324.0e6,
+}
 
 
 SMS, FP32_LANES_PER_SM = 152, 128          # GB300: 152 SMs x 4 partitions x 32 FP32 lanes
@@ -532,7 +541,7 @@ def roofline_record(prof, dom, wl, peaks, sm_mhz, gram_tensor, apps):
         "greenq": "2 x n x 8 B per column + the Green symbol of each pole",
         "orth": "(2(k+1) + 3) x n x 8 B per active system at Arnoldi step k",
     }.get(dom, "the library's algorithmic byte count")
-    tr = TRAFFIC_PER_CALL.get(dom)
+    tr = TRAFFIC_PER_CALL.get((getattr(wl, "name", None), N, dom))
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": tr,
             "algorithmic_bytes_per_call": per_call,
@@ -604,14 +613,20 @@ def run_many(a):
     import numpy as np
     import torch
     from paper_1603_09724_gb300.serve import OmmServer, Request, latency_summary
-    from workloads import batch_mix, serving_mix, poisson_arrivals
+    from workloads import batch_mix, serving_mix, serving_mix_3d, serving_mix_wide, poisson_arrivals
+    import paper_1603_09724_gb300 as omm
     spectra = json.load(open(os.path.join(ROOT, "workloads", "spectra.json")))
     specs = batch_mix() if a.mode == "batch" else serving_mix()
+    if a.mode == "serve" and a.mix == "full":
+        specs = specs + serving_mix_wide() + serving_mix_3d()
 
     def request(h):
         sp = spectra[h.key]
-        return Request(h.key, 2, h.m, h.L, h.potential_values(), sp["N"], sp["lam1"], sp["lamN"], sp["lamN1"],
-                       sigma=sp["sigma"], P=16)
+        dim = getattr(h, "dim", 2)
+        # the sparsifying factor is built up to 16^3 in 3D; larger 3D grids take the kinetic inner preconditioner
+        params = {"inner": omm.OMM_INNER_KINETIC} if dim == 3 and h.m > 16 else None
+        return Request(h.key, dim, h.m, h.L, h.potential_values(), sp["N"], sp["lam1"], sp["lamN"], sp["lamN1"],
+                       sigma=sp["sigma"], P=16, params=params)
 
     free, total = torch.cuda.mem_get_info()
     srv = OmmServer(hbm_budget=int(0.85 * free), slots=a.slots, gmres_rtol=a.rtol,
@@ -645,7 +660,10 @@ def run_many(a):
         res = srv.drain(a.requests)
         wall = time.perf_counter() - t0
         extra = {"arrival_rate_per_s": a.rate}
-        cfg = f"Poisson arrivals ({a.rate:g}/s) over {len(specs)} 2D Gaussian-well Hamiltonians, grids from {{64,72,96,128}}^2, N in [32,128]"
+        cfg = (f"Poisson arrivals ({a.rate:g}/s) over {len(specs)} Hamiltonians: 2D Gaussian wells on "
+               f"{{64,72,96,128}}^2 with N in [32,128]" +
+               (", four more 2D ones with N in [129,256], and the 3D well lattice on 32^3 (N = 64) and "
+                "48^3 (N = 64 and 256), with the kinetic inner preconditioner above 16^3" if a.mix == "full" else ""))
     clk = clocks.stop()
     summ = latency_summary(res, wall)
     failed = [r.error for r in res if r.error is not None]
@@ -665,10 +683,67 @@ def run_many(a):
     print(json.dumps(rec))
 
 
+def run_graph(a):
+    """The 64-Hamiltonian batch mix solved by one CUDA-graph launch (paper_1603_09724_gb300.
+    batch): fixed CG schedule (20 iterations), one GMRES cycle of 12 steps with the systems
+    that meet rtol 1e-5 masked on the device, real orbitals, mixed; the launch schedule of
+    every shape chosen by the autotuner; the timed region is `steps` replays of the graph;
+    one JSON line."""
+    import tempfile
+    import numpy as np
+    import torch
+    from paper_1603_09724_gb300 import batch
+    from workloads import batch_mix
+    spectra = json.load(open(os.path.join(ROOT, "workloads", "spectra.json")))
+    insts = []
+    for i, h in enumerate(batch_mix()):
+        sp = spectra[h.key]
+        insts.append(batch.Instance(h.key, 2, h.m, h.L, h.potential_values(), sp["N"], sp["lam1"], sp["lamN"],
+                                    sp["lamN1"], sigma=sp["sigma"], seed=i))
+    schedule = dict(precision=1, real_orbitals=1, fixed_iters=20, gmres_m=12, gmres_cycles=1, tol=1e-10)
+    tune_path = os.path.join(tempfile.mkdtemp(), "omm_tune.json")
+    tuner = batch.Autotuner(tune_path)
+    t0 = time.perf_counter()
+    gb = batch.GraphBatch(insts, schedule, autotuner=tuner)
+    gb.setup()
+    gb.capture()
+    setup_s = time.perf_counter() - t0
+    for _ in range(max(a.warmup, 1)):
+        res = gb.run()
+    clocks = ClockSampler(0)
+    clocks.start()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(a.steps):
+        gb.graph.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    res = [s.read_result() for _, s, _, _ in gb.items]
+    errs = [abs(r["energy_fp64"] - spectra[i.key]["E_ref"]) / abs(spectra[i.key]["E_ref"]) for i, r in zip(insts, res)]
+    rec = {"mode": "graph", "metric": METRIC, "value": len(insts) * a.steps / (ms / 1000.0), "unit": "solves/s",
+           "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": f"{len(insts)} independent 2D Hamiltonians, grids from {{32,64,96,128}}^2, N in "
+                                  "[16,128], smooth random V; one CUDA-graph launch per step solves all of them",
+                      "schedule": schedule, "autotuned": {k: v["params"] for k, v in tuner.table.items()},
+                      "l2": "working set (all instances' GMRES bases) far larger than L2"},
+           "gpu_launches": 1, "graph_launches_per_step": 1,
+           "setup_s": setup_s, "E_rel_err_vs_exact": {"max": max(errs), "median": float(np.median(errs))},
+           "clocks": clk}
+    gb.close()
+    print(json.dumps(rec))
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "graph":
+        run_graph(a)
     elif a.mode != "solve":
         run_many(a)
     else:

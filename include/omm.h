@@ -221,6 +221,26 @@ omm_status omm_iterate(omm_t h, int k, omm_stats* st);
  * further rounds run); OMM_ESTATE if neither poles nor gTPA are set. */
 omm_status omm_solve(omm_t h, omm_stats* st);
 
+/* The solve of omm_solve with a fixed schedule, enqueued on the handle's stream without
+ * any host synchronisation, host copy or allocation, so that it can be captured in a CUDA
+ * graph (stream capture) and replayed, alone or with the solves of other handles on
+ * their own streams (no counterpart in the paper: the batched form of many Hamiltonians).
+ * Needs fixed_iters > 0 (every CG round runs exactly that many iterations); every GMRES
+ * cycle runs all gmres_m steps, and unless gmres_fixed = 1 the systems that meet the
+ * tolerance are masked on the device from then on (their kernels return at once).  The
+ * handle's work space must exist: call omm_solve once first.  The energy criterion is not tested (st->converged of omm_read_result
+ * reports whether the last step met it).  Results stay on the device until
+ * omm_read_result.
+ * Errors: OMM_EINVAL (fixed_iters not set), OMM_ESTATE (no poles / gTPA, or no prior
+ * omm_solve), OMM_ECUDA. */
+omm_status omm_solve_enqueue(omm_t h);
+/* Synchronises the handle's stream and returns the statistics of the last
+ * omm_solve_enqueue (iterations, filters, energies, FP64 residuals, angle bound, GMRES
+ * statistics of the last pole solve).
+ * Errors: OMM_ESTATE (nothing enqueued), OMM_ESHIFT (the quartic was not bounded below),
+ * OMM_ENOTCONV (a non-finite energy, step or beta), OMM_ETIMEOUT, OMM_ECUDA. */
+omm_status omm_read_result(omm_t h, omm_stats* st);
+
 /* E_omm (eq. omm) of the current X evaluated in FP64 (FP64 H-apply and FP64 Grams).
  * Errors: OMM_EINVAL (NULL handle or E), OMM_ENOMEM (first call allocates the FP64
  * work space), OMM_ECUDA. */

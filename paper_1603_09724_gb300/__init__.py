@@ -71,6 +71,8 @@ _SIGS = {
     "omm_iterate": (C.c_int, [_vp, C.c_int, C.POINTER(omm_stats)]),
     "omm_solve": (C.c_int, [_vp, C.POINTER(omm_stats)]),
     "omm_energy": (C.c_int, [_vp, _dp]),
+    "omm_solve_enqueue": (C.c_int, [_vp]),
+    "omm_read_result": (C.c_int, [_vp, C.POINTER(omm_stats)]),
     "omm_apply_h": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double]),
     "omm_gram": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _vp]),
     "omm_gradient": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -236,6 +238,18 @@ class Solver:
         s = lib.omm_solve(self.h, C.byref(st))
         if not (s == OMM_OK or (allow_notconv and s == OMM_ENOTCONV)):
             check(s, "omm_solve")
+        return st.as_dict()
+
+    def solve_enqueue(self):
+        """Enqueue a fixed-schedule solve without host synchronisation (capturable in a CUDA
+        graph); read it with read_result()."""
+        check(lib.omm_solve_enqueue(self.h), "omm_solve_enqueue")
+
+    def read_result(self, allow_notconv=True):
+        st = omm_stats()
+        s = lib.omm_read_result(self.h, C.byref(st))
+        if not (s == OMM_OK or (allow_notconv and s == OMM_ENOTCONV)):
+            check(s, "omm_read_result")
         return st.as_dict()
 
     def energy(self):

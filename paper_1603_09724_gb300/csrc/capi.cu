@@ -119,6 +119,9 @@ struct omm_ctx {
   // is likewise reset before its buffer is replaced)
   bool fp64_ready = false, ghat_ready = false, proj_ready = false;
   bool breakdown = false;       // the last CG run met a non-finite energy / step / beta
+  bool enqueue_only = false;    // omm_solve_enqueue: no host synchronisation, results stay on the device
+  double2* sigma64 = nullptr;   // (sigma, 0) on the device for the FP64 check
+  bool enqueued = false;        // results of an omm_solve_enqueue are waiting on the device
 
   // poles
   int P = 0;
@@ -620,6 +623,10 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
   auto Zk = [&](int k) { return (void*)((char*)h->Zb + (size_t)k * vs); };
   const double rtol = h->cur_rtol;
   const int fixed = h->prm.gmres_fixed;
+  // the host reads the active counts to stop early, except when the solve is only being
+  // enqueued: then every cycle runs all its steps, and systems that met the tolerance are
+  // masked on the device (their kernels return at once)
+  const bool host_checks = !fixed && !h->enqueue_only;
   OMM_TRY(cuda_status(cudaMemsetAsync(h->itot, 0, sizeof(int) * d.S, h->st), "memset"));
   for (int cyc = 0; cyc < h->prm.gmres_cycles; ++cyc) {
     h->nact_last = -1;   // every system until the cycle start has been counted
@@ -638,7 +645,7 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
                        "restart"));
     }
     double cyc_cols = d.S;   // systems the cycle works on (for the update's bytes)
-    if (!fixed) {
+    if (host_checks) {
       // count active systems after the cycle start
       PROF(PC_SMALL, 0, 1, cuda_status(launch_count_active(d, h->active, h->nact_d, h->st), "count"));
       int na = 0;
@@ -658,7 +665,7 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
            cuda_status(launch_krylov_givens(d, k, h->Hh, h->cs, h->gv, h->bnorm, h->active, h->steps, h->est, rtol,
                                             fixed, h->nact_d, h->st),
                        "givens"));
-      if (!fixed && k + 1 < d.m) {
+      if (host_checks && k + 1 < d.m) {
         int na = 0;
         OMM_TRY(read_nactive(h, &na));
         if (na == 0) break;
@@ -806,6 +813,7 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
     PROF(PC_VEC, 3.0 * cnt * h->csz, 1,
          cuda_status(launch_axpby(h->dbl, cnt, &h->sc->t_c, h->HD(), &h->sc->one_c, h->HX(), h->st), "upd"));
     std::swap(h->G, h->Gp);
+    if (h->enqueue_only) continue;   // fixed schedule: no host decision until the results are read
     OMM_TRY(read_scalars(h));
     if (!h->use_proj && !h->use_gtpa) {
       OMM_TRY(gmres_stats(h));
@@ -863,6 +871,10 @@ omm_status energy_fp64(omm_ctx* h, double* E, double* resid, double* resid_orth 
     // N x N: R, R^-1, T, -S^-1 K, zeros; then E, three norms, the Cholesky flag
     OMM_TRY(h->dalloc(&h->m64, 5 * nn * 16 + 4 * sizeof(double) + sizeof(int)));
     OMM_TRY(cuda_status(cudaMemsetAsync((char*)h->m64 + 4 * nn * 16, 0, nn * 16, h->st), "memset"));
+    OMM_TRY(h->dalloc_t(&h->sigma64, sizeof(double2)));
+    const double2 sg = make_double2(h->shift, 0.0);
+    OMM_TRY(cuda_status(cudaMemcpyAsync(h->sigma64, &sg, sizeof(sg), cudaMemcpyHostToDevice, h->st), "sigma"));
+    OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "sync"));
     h->fp64_ready = true;
   }
   void* X64 = h->X64;
@@ -880,9 +892,7 @@ omm_status energy_fp64(omm_ctx* h, double* E, double* resid, double* resid_orth 
     OMM_TRY(cuda_status(cudaMemcpyAsync(X64, h->X(), cnt * 16, cudaMemcpyDeviceToDevice, h->st), "copy"));
   else
     PROF(PC_VEC, 24.0 * cnt, 1, cuda_status(launch_convert(true, cnt, h->X(), X64, h->st), "convert"));
-  const double2 sh = make_double2(h->shift, 0.0);
-  OMM_TRY(cuda_status(cudaMemcpyAsync(h->tmp_shift, &sh, sizeof(sh), cudaMemcpyHostToDevice, h->st), "shift"));
-  OMM_TRY(happly(h, X64, HX64, N, h->tmp_shift, N, nullptr, true));
+  OMM_TRY(happly(h, X64, HX64, N, h->sigma64, N, nullptr, true));
   PROF(PC_GRAM, 3.0 * cnt * 16, 2,
        cuda_status(launch_gram(true, X64, N, X64, 2 * N, h->n, h->gram64, 2 * N, h->gram64_work, h->st), "gram64"));
   PROF(PC_SMALL, 0, 3,
@@ -896,6 +906,7 @@ omm_status energy_fp64(omm_ctx* h, double* E, double* resid, double* resid_orth 
     PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, X64, X64, dres + 2, h->red_work, h->st), "dot"));
     PROF(PC_VEC, 2.0 * cnt * 16, 2, cuda_status(launch_redot(true, cnt, Q64, Q64, dres + 3, h->red_work, h->st), "dot"));
   }
+  if (h->enqueue_only) return OMM_OK;   // read by omm_read_result
   double out[4] = {0.0, 0.0, 0.0, 0.0};
   int ok = 0;
   OMM_TRY(cuda_status(cudaMemcpyAsync(out, dres, sizeof(out), cudaMemcpyDeviceToHost, h->st), "d2h"));
@@ -1366,6 +1377,72 @@ omm_status omm_solve(omm_t h, omm_stats* st) {
   }
   if (st) *st = loc;
   return conv ? OMM_OK : OMM_ENOTCONV;
+}
+
+omm_status omm_solve_enqueue(omm_t h) {
+  if (!h) return OMM_EINVAL;
+  if (!h->poles_set && !h->use_gtpa) return OMM_ESTATE;
+  if (h->prm.fixed_iters < 1) {
+    omm_internal_set_message("omm_solve_enqueue needs fixed_iters > 0 (a fixed CG schedule)");
+    return OMM_EINVAL;
+  }
+  if (!h->fp64_ready || !h->gram || (h->prm.gram_tensor && !h->dbl && !h->tc_err)) {
+    omm_internal_set_message("omm_solve_enqueue: call omm_solve once first (it allocates the work space)");
+    return OMM_ESTATE;
+  }
+  h->enqueue_only = true;
+  h->gmres_total = 0;
+  omm_status s = OMM_OK;
+  const int rounds = h->use_gtpa ? 0 : h->prm.refilter;
+  for (int round = 0; round <= rounds && s == OMM_OK; ++round) {
+    h->cur_rtol = (round > 0 && h->prm.refilter_rtol > 0.0) ? h->prm.refilter_rtol : h->prm.gmres_rtol;
+    if (!h->use_gtpa) s = omm_filter(h);
+    int done = 0;
+    bool conv = false;
+    if (s == OMM_OK) s = cg_steps(h, h->prm.fixed_iters, nullptr, &done, &conv);
+  }
+  if (s == OMM_OK) {
+    double E = 0.0, r = 0.0, ro = 0.0;
+    s = energy_fp64(h, &E, &r, &ro);
+  }
+  h->cur_rtol = h->prm.gmres_rtol;
+  h->enqueue_only = false;
+  h->enqueued = s == OMM_OK;
+  return s;
+}
+
+omm_status omm_read_result(omm_t h, omm_stats* st) {
+  if (!h || !st) return OMM_EINVAL;
+  if (!h->enqueued) return OMM_ESTATE;
+  std::memset(st, 0, sizeof(*st));
+  const int N = h->N;
+  const size_t nn = (size_t)N * N;
+  const double* dres = (const double*)((double2*)h->m64 + 5 * nn);
+  double out[4] = {0.0, 0.0, 0.0, 0.0};
+  int ok = 0;
+  OMM_TRY(cuda_status(cudaMemcpyAsync(out, dres, sizeof(out), cudaMemcpyDeviceToHost, h->st), "d2h"));
+  OMM_TRY(cuda_status(cudaMemcpyAsync(&ok, dres + 4, sizeof(int), cudaMemcpyDeviceToHost, h->st), "d2h"));
+  OMM_TRY(read_scalars(h));
+  if (!h->use_proj && !h->use_gtpa) OMM_TRY(gmres_stats(h));
+  const int rounds = h->use_gtpa ? 0 : h->prm.refilter;
+  st->iters = h->prm.fixed_iters * (rounds + 1);
+  st->filters = h->use_gtpa ? 0 : rounds + 1;
+  st->energy = h->sc_h->E1;
+  st->grad_norm = std::sqrt(std::max(h->sc_h->grad2, 0.0));
+  st->energy_fp64 = out[0];
+  st->resid_fp64 = ok ? std::sqrt(out[1] / std::max(out[2], 1e-300)) : std::nan("");
+  st->resid_orth = ok ? std::sqrt(out[3]) : std::nan("");
+  st->angle_bound = h->prm.gap > 0.0 ? st->resid_orth / h->prm.gap : 0.0;
+  st->gmres_iters_max = h->last_gmres_max;
+  st->gmres_relres_max = h->last_relres_max;
+  const bool finite = std::isfinite(h->sc_h->E1) && std::isfinite(h->sc_h->t) && std::isfinite(h->sc_h->beta);
+  st->converged = finite && !h->sc_h->bad && h->sc_h->converged;
+  if (h->sc_h->bad) return OMM_ESHIFT;
+  if (!finite) {
+    omm_internal_set_message("non-finite energy, line-search step or beta in the CG");
+    return OMM_ENOTCONV;
+  }
+  return OMM_OK;
 }
 
 omm_status omm_energy(omm_t h, double* E) {

@@ -426,13 +426,28 @@ constexpr int LDY = LT + 1;   // padded stride: the leaf-index-fastest accesses 
 constexpr int LNB = 9;        // couplings per row of F_BS / F_SB (3^2 stencil)
 constexpr int LGB = 8;        // gathered loads in flight per thread
 
+// Band substitutions, one right-hand side per thread on its column of y (stride LDY).
+// The band loops are unrolled to kMaxBw with the rows near the ends predicated, and each
+// term is two fused multiply-adds per component (acc - l y), so a row costs about 4 bw FMA
+// instructions and no loop control.
+constexpr int kMaxBw = 9;   // leaves of at most 8 x 8 points (x-fastest order: band <= 9)
+
+template <typename C>
+__device__ __forceinline__ C cfms(C l, C y, C acc) {   // acc - l * y
+  acc.x = fma(-l.x, y.x, fma(l.y, y.y, acc.x));
+  acc.y = fma(-l.x, y.y, fma(-l.y, y.x, acc.y));
+  return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ void band_lower(cx_t<T>* y, int ns, int bw, const cx_t<T>* Lb) {
   for (int i = 0; i < ns; ++i) {
     cx_t<T> acc = y[i * LDY];
     const cx_t<T>* lr = Lb + i * bw;
     const int tn = min(bw, i);
-    for (int t = 0; t < tn; ++t) acc = csub(acc, cmul(lr[t], y[(i - 1 - t) * LDY]));
+#pragma unroll
+    for (int t = 0; t < kMaxBw; ++t)
+      if (t < tn) acc = cfms(lr[t], y[(i - 1 - t) * LDY], acc);
     y[i * LDY] = acc;
   }
 }
@@ -443,7 +458,9 @@ __device__ __forceinline__ void band_upper(cx_t<T>* y, int ns, int bw, const cx_
     cx_t<T> acc = y[i * LDY];
     const cx_t<T>* ur = Ub + i * (bw + 1);
     const int tn = min(bw, ns - 1 - i);
-    for (int t = 1; t <= tn; ++t) acc = csub(acc, cmul(ur[t], y[(i + t) * LDY]));
+#pragma unroll
+    for (int t = 1; t <= kMaxBw; ++t)
+      if (t <= tn) acc = cfms(ur[t], y[(i + t) * LDY], acc);
     y[i * LDY] = cmul(ur[0], acc);
   }
 }
@@ -697,6 +714,7 @@ static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, co
     if (e != cudaSuccess) return e;
   }
   const bool leaves = la.nleaves > 0;
+  if (leaves && la.bw > kMaxBw) return cudaErrorInvalidValue;   // the unrolled band loops cover kMaxBw
   const size_t lsm = leaf_smem_bytes<T>(la.max_ns, la.max_nb, la.bw);
   const dim3 lgrid((a.N + LT - 1) / LT, la.nleaves, P);
   if (leaves && (phases & SPP_LEAF_FWD)) {

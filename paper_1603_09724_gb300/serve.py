@@ -40,6 +40,8 @@ class Request:
     X0: Optional[np.ndarray] = None   # host (N, n) starting block; random if None and cold
     arrival: float = 0.0              # seconds (time.perf_counter scale), set by submit()
     rid: int = -1
+    params: Optional[dict] = None     # omm_params overrides for this Hamiltonian's handle
+                                      # (e.g. the inner preconditioner of a large 3D grid)
 
 
 @dataclasses.dataclass
@@ -166,7 +168,8 @@ class OmmServer:
 
     # ---------------------------------------------------------------- internals
     def _shape(self, req: Request):
-        return (req.dim, req.m, req.N, req.P, self.params.get("precision"))
+        return (req.dim, req.m, req.N, req.P, self.params.get("precision"),
+                tuple(sorted((req.params or {}).items())))
 
     def _estimate(self, req: Request) -> int:
         """Footprint of a handle: measured for a shape seen before, else the GMRES work
@@ -235,7 +238,7 @@ class OmmServer:
                 s = None
                 try:
                     with dev.stream_ctx(stream):
-                        prm = omm.default_params(**self.params)
+                        prm = omm.default_params(**{**self.params, **(req.params or {})})
                         s = omm.Solver(req.dim, req.m, req.L, req.V, req.N, shift=req.sigma, params=prm,
                                        stream=dev.stream_handle(stream))
                         z, w = omm.poles_fermi(req.lam1, req.lamN, req.lamN1, req.P)

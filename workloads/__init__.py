@@ -161,16 +161,23 @@ class HamSpec:
     m: int
     N: int
     L: float
-    potential: str     # 'smooth2d' | 'wells2d'
+    potential: str     # 'smooth2d' | 'wells2d' | 'lattice3d'
     seed: int
+    dim: int = 2
 
     @property
     def n(self) -> int:
-        return self.m * self.m
+        return self.m ** self.dim
+
+    @property
+    def shape(self) -> tuple:
+        return (self.m,) * self.dim
 
     def potential_values(self) -> np.ndarray:
         if self.potential == "smooth2d":
             return smooth_field_2d(self.m, self.L, seed=self.seed)
+        if self.potential == "lattice3d":
+            return lattice_wells_3d(self.m, self.L)
         return wells_2d(self.m, self.L, seed=self.seed)
 
 
@@ -197,6 +204,27 @@ def serving_mix(count: int = 12, seed: int = 1) -> list:
         N = int(rng.integers(32, 129))
         out.append(HamSpec(f"serve{i}", m, N, 10.0, "wells2d", 200 + i))
     return out
+
+
+def serving_mix_wide(count: int = 4, seed: int = 3) -> list:
+    """More served 2D Hamiltonians, with N uniform in [129, 256] (at most n/4): grids from
+    {64, 96, 128}^2, four Gaussian wells per box (seed 220 + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.choice([64, 96, 128]))
+        N = min(int(rng.integers(129, 257)), m * m // 4)
+        out.append(HamSpec(f"serve-wide{i}", m, N, 10.0, "wells2d", 220 + i))
+    return out
+
+
+def serving_mix_3d() -> list:
+    """Served 3D Hamiltonians: the 4^3 lattice of Gaussian wells of the 48^3 workload (box
+    L = 40) on a 32^3 grid with N = 64 (the s band; its p band is not separated from the
+    next states at 8 points per cell) and on 48^3 with N = 64 and N = 256 (s and p bands)."""
+    return [HamSpec("serve3d-32", 32, 64, 40.0, "lattice3d", 300, 3),
+            HamSpec("serve3d-48s", 48, 64, 40.0, "lattice3d", 301, 3),
+            HamSpec("serve3d-48", 48, 256, 40.0, "lattice3d", 302, 3)]
 
 
 def poisson_arrivals(count: int, rate: float, nkeys: int, seed: int = 2):

@@ -19,7 +19,7 @@ import numpy as np
 
 from oracle import gtpa, hamiltonian as ham
 from oracle import spectrum
-from workloads import WORKLOADS, batch_mix, serving_mix
+from workloads import WORKLOADS, batch_mix, serving_mix, serving_mix_3d, serving_mix_wide
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "spectra.json")
 
@@ -55,22 +55,26 @@ def gtpa_tau(wl, sig, kc=24):
 
 
 def compute_spec(h, kc=24, window=8):
-    """Spectral data of one many-Hamiltonian entry (dense eigh for n <= 4096, else the
-    plane-wave box).  N is taken within +-window of the drawn value where the gap
+    """Spectral data of one many-Hamiltonian entry (dense eigh for n <= 4096, the Bloch
+    sectors for the 3D lattice, else the plane-wave box).  N is taken within +-window of the drawn value where the gap
     lam_{N+1} - lam_N is largest, so that the occupied space is well separated."""
     V = h.potential_values()
-    shape = (h.m, h.m)
+    shape = h.shape
     sig = ham.default_shift(shape, h.L, V)
+    if h.potential == "lattice3d":
+        window = 0                   # N is the band edge of the lattice (64: s, 256: s + p)
     cnt = h.N + window + 1
     if h.n <= 4096:
         lam = np.linalg.eigvalsh(ham.dense_h(shape, h.L, V, sig))[:cnt]
+    elif h.potential == "lattice3d":
+        lam = spectrum.lowest_eigs_bloch(shape, h.L, V, sig, 4, cnt)
     else:
         lam = spectrum.lowest_eigs_kspace(shape, h.L, V, sig, cnt, kc)
     cands = range(max(1, h.N - window), h.N + window + 1)
     N = max(cands, key=lambda k: lam[k] - lam[k - 1])
     return dict(sigma=sig, lam1=float(lam[0]), lamN=float(lam[N - 1]), lamN1=float(lam[N]),
                 E_ref=float(0.5 * np.sum(lam[:N])), m=h.m, N=int(N), N_drawn=h.N, potential=h.potential,
-                seed=h.seed)
+                seed=h.seed, dim=h.dim)
 
 
 def main(names=("wells2d-32", "smooth2d-128", "lattice3d-48")):
@@ -87,7 +91,7 @@ def main(names=("wells2d-32", "smooth2d-128", "lattice3d-48")):
         if wl.dim == 2 and "gtpa_tau" not in data[name]:
             data[name]["gtpa_tau"] = gtpa_tau(wl, data[name]["sigma"])
             print(name, "tau", data[name]["gtpa_tau"])
-    for h in batch_mix() + serving_mix():
+    for h in batch_mix() + serving_mix() + serving_mix_wide() + serving_mix_3d():
         if h.key not in data:
             data[h.key] = compute_spec(h)
             print(h.key, h.m, h.N, data[h.key]["lamN1"] - data[h.key]["lamN"], flush=True)

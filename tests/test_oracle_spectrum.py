@@ -84,3 +84,22 @@ def test_lattice_workload_is_cell_periodic():
     mc = m // cells
     for ax in range(3):
         np.testing.assert_allclose(np.roll(V, mc, axis=ax), V, atol=1e-12)
+
+
+def test_stored_spectrum_of_the_served_32_lattice():
+    """The stored spectral data of the served 32^3 lattice (N = 64, the s band) are those of
+    the Bloch solver: lam_1, lam_N, lam_{N+1} and 1/2 sum_{i<=N} lam_i, with a clear gap."""
+    import json
+    import os
+    from workloads import serving_mix_3d
+    h = serving_mix_3d()[0]
+    stored = json.load(open(os.path.join(os.path.dirname(__file__), "..", "workloads", "spectra.json")))[h.key]
+    V = h.potential_values()
+    lam = spectrum.lowest_eigs_bloch(h.shape, h.L, V, stored["sigma"], 4, h.N + 1)
+    scale = abs(stored["lam1"])
+    assert stored["N"] == h.N == 64
+    assert abs(lam[0] - stored["lam1"]) < 1e-11 * scale
+    assert abs(lam[h.N - 1] - stored["lamN"]) < 1e-11 * scale
+    assert abs(lam[h.N] - stored["lamN1"]) < 1e-11 * scale
+    assert abs(0.5 * lam[:h.N].sum() - stored["E_ref"]) < 1e-11 * abs(stored["E_ref"])
+    assert stored["lamN1"] - stored["lamN"] > 1.0

@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from workloads import (WORKLOADS, batch_mix, gaussian_block, gaussian_block_real, lattice_wells_3d,
-                       poisson_arrivals, serving_mix, smooth_field_2d, wells_2d)
+                       poisson_arrivals, serving_mix, serving_mix_3d, serving_mix_wide, smooth_field_2d,
+                       wells_2d)
 
 
 def test_smooth_field_is_band_limited_with_the_stated_envelope():
@@ -78,3 +79,11 @@ def test_mixes_and_arrivals_have_the_stated_ranges():
     assert 4000 / t[-1] == pytest.approx(200.0, rel=0.05)
     w = WORKLOADS["smooth2d-128"]
     assert (w.dim, w.m, w.N, w.P, w.L, w.precision) == (2, 128, 128, 16, 10.0, "mixed")
+    wide = serving_mix_wide()
+    assert len(wide) == 4 and {h.m for h in wide} <= {64, 96, 128}
+    assert all(129 <= h.N <= min(256, h.m * h.m // 4) and h.potential == "wells2d" and h.dim == 2 for h in wide)
+    s3 = serving_mix_3d()
+    assert [(h.dim, h.m, h.N, h.L, h.potential) for h in s3] == [
+        (3, 32, 64, 40.0, "lattice3d"), (3, 48, 64, 40.0, "lattice3d"), (3, 48, 256, 40.0, "lattice3d")]
+    assert s3[0].n == 32 ** 3 and s3[0].shape == (32, 32, 32)
+    np.testing.assert_array_equal(s3[2].potential_values(), WORKLOADS["lattice3d-48"].potential_values())

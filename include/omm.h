@@ -119,6 +119,18 @@ typedef struct {
                            reports the Davis-Kahan bound resid_orth / gap on the sine of
                            the largest principal angle to the exact invariant subspace;
                            0: not reported                                             */
+  int launch_overlap;   /* 1 (default): the launches of the triangular solves are
+                           programmatic dependent launches: each one is scheduled while
+                           the one before it on its stream runs, loads its factor values
+                           and index lists, and waits for that launch's results only
+                           before it reads them; 0: ordinary launches                 */
+  int device_factor;    /* 1 (default): omm_set_poles factors the sparsifying matrix P of
+                           every pole on the device (multifrontal LU height by height,
+                           all fronts of a height and all poles per launch, in the
+                           handle's precision); the host computes only each pole's
+                           stencil q (Sec. 3.2, eq. QG).  0: the host factorisation in
+                           FP64 (rounded to the handle's precision), as before.  Grids
+                           too small for the stencil use the host factorisation.       */
 } omm_params;
 
 typedef struct {
@@ -147,7 +159,8 @@ const char* omm_last_error_message(void);
 
 /* Defaults: FP64, sparsifying inner preconditioner, GMRES(15) x 5 cycles, rtol 1e-5
  * (Sec. 4), stencil radius 1, pivot floor 1e-12, tol 1e-13, maxit 50, no refilter,
- * trsv_persistent 0, fixed_iters 0, refilter_rtol 0 (= gmres_rtol), gap 0 (no angle bound).
+ * trsv_persistent 0, fixed_iters 0, refilter_rtol 0 (= gmres_rtol), gap 0 (no angle bound),
+ * launch_overlap 1, device_factor 1.
  * Errors: OMM_EINVAL (p NULL). */
 omm_status omm_default_params(omm_params* p);
 

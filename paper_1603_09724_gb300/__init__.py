@@ -36,7 +36,7 @@ class omm_params(C.Structure):
                 ("pivot_floor", C.c_double), ("tol", C.c_double), ("maxit", C.c_int), ("refilter", C.c_int),
                 ("gram_tensor", C.c_int), ("real_orbitals", C.c_int), ("trsv_streams", C.c_int),
                 ("trsv_persistent", C.c_int), ("fixed_iters", C.c_int), ("refilter_rtol", C.c_double),
-                ("gap", C.c_double)]
+                ("gap", C.c_double), ("launch_overlap", C.c_int), ("device_factor", C.c_int)]
 
 
 class omm_stats(C.Structure):

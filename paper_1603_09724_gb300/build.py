@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libomm.so")
 
 CUDA_UNITS = ["capi.cu", "k_fft.cu", "k_fft_big.cu", "k_blas.cu", "k_gram_tc.cu", "k_small.cu", "k_krylov.cu",
-              "k_trsv.cu"]
+              "k_trsv.cu", "k_factor.cu"]
 CXX_UNITS = ["host_poles.cpp", "host_spp.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

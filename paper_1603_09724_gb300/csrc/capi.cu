@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "factor.h"
 #include "kernels.h"
 #include "spp.h"
 #include "trsv.h"
@@ -195,6 +196,16 @@ struct omm_ctx {
   int* d_bblocks = nullptr;
   int* d_lunk = nullptr;                    // unknowns of each tree height (ND indices)
   unsigned* d_trsv_bar = nullptr;           // grid barrier of the persistent level launch: count, generation, error
+  // device factorisation of P (k_factor.cu): maps built once per handle
+  bool fmaps_tried = false, fmaps_ok = false;
+  long long front_size = 0;                 // front entries per pole
+  long long* d_foff = nullptr;
+  int *d_child0 = nullptr, *d_child1 = nullptr, *d_asm_ptr = nullptr, *d_asm_pos = nullptr, *d_asm_src = nullptr;
+  int *d_nbr = nullptr, *d_emap = nullptr, *d_leaf_of = nullptr, *d_hnodes = nullptr;
+  double* d_Vdbl = nullptr;
+  double2* d_qq = nullptr;                  // PMAX x 27 (q) then PMAX x 27 ((qG)(0, a))
+  std::vector<int> hn_start, hn_count, hn_tiles;   // per height: nodes and W-product tiles
+  bool last_factor_device = false;
   // algorithmic complex elements of the triangular-solve phases: per system and per pole
   double tb_leaf_fwd_sys = 0, tb_leaf_bwd_sys = 0, tb_leaf_pole = 0, tb_lvl_sys = 0, tb_lvl_pole = 0;
   double n_leaf = 0, n_sep = 0;   // unknowns in the leaves / in the separators (algorithmic bytes)
@@ -251,6 +262,16 @@ struct omm_ctx {
     if (nact_h) cudaFreeHost(nact_h);
   }
 
+  // a work buffer that does not outlive the call: freed again by dfree (same size)
+  void dfree(void* p, size_t b) {
+    auto it = std::find(allocs.begin(), allocs.end(), p);
+    if (!p || it == allocs.end()) return;
+    allocs.erase(it);
+    if (release) release(p, alloc_ctx);
+    else cudaFree(p);
+    if (b == 0) b = 16;
+    bytes -= (b + 255) / 256 * 256;
+  }
   omm_status dalloc(void** p, size_t b) {
     *p = nullptr;
     if (b == 0) b = 16;
@@ -562,7 +583,7 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
     }
     if (ng == 1 || (h->prm.trsv_persistent && phases != (SPP_LEVELS_FWD | SPP_LEVELS_BWD)))
       return cuda_status(launch_spp_solve(phases, h->dbl, a, lv, la, P, tmp, h->ynd, h->ubuf, Z, h->xnd, h->factor,
-                                          active, h->trsv_smem, h->st),
+                                          active, h->trsv_smem, h->prm.launch_overlap, h->st),
                          "spp");
     OMM_TRY(cuda_status(cudaEventRecord(h->ev_fork, h->st), "fork"));
     int p0 = 0;
@@ -576,7 +597,7 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
                            (char*)h->ynd + vec0, (char*)h->ubuf + sys0 * h->csz, (char*)Z + vec0,
                            (char*)h->xnd + vec0,
                            (const char*)h->factor + (size_t)p0 * h->spp.factor_size * h->csz,
-                           active ? active + sys0 : nullptr, h->trsv_smem, h->st2[g]),
+                           active ? active + sys0 : nullptr, h->trsv_smem, h->prm.launch_overlap, h->st2[g]),
           "spp"));
       OMM_TRY(cuda_status(cudaEventRecord(h->ev_join[g], h->st2[g]), "join"));
       OMM_TRY(cuda_status(cudaStreamWaitEvent(h->st, h->ev_join[g], 0), "join"));
@@ -1037,6 +1058,8 @@ omm_status omm_default_params(omm_params* p) {
   p->trsv_persistent = 0;
   p->refilter_rtol = 0.0;
   p->gap = 0.0;
+  p->launch_overlap = 1;
+  p->device_factor = 1;
   return OMM_OK;
 }
 
@@ -1077,7 +1100,8 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
   if (p) prm = *p;
   if (prm.gmres_m < 1 || prm.gmres_m > 15 || prm.gmres_cycles < 1 || prm.maxit < 0 || prm.refilter < 0 ||
       (prm.precision != OMM_FP64 && prm.precision != OMM_MIXED) || prm.inner < 0 || prm.inner > 2 ||
-      prm.trsv_persistent < 0 || prm.trsv_persistent > 1 ||
+      prm.trsv_persistent < 0 || prm.trsv_persistent > 1 || prm.launch_overlap < 0 || prm.launch_overlap > 1 ||
+      prm.device_factor < 0 || prm.device_factor > 1 ||
       prm.stencil_radius != 1 || prm.trsv_streams < 0 || prm.trsv_streams > omm_ctx::kTrsvStreams ||
       !(prm.gmres_rtol >= 0.0) || !std::isfinite(prm.gmres_rtol) || !(prm.tol >= 0.0) || !std::isfinite(prm.tol) ||
       !(prm.pivot_floor >= 0.0) || !std::isfinite(prm.pivot_floor) || !std::isfinite(shift) || prm.fixed_iters < 0 ||
@@ -1198,6 +1222,140 @@ static bool fold_conjugate_pairs(int P, const double* z, const double* w, std::v
   return true;
 }
 
+// Maps of the device factorisation (once per handle); leaves fmaps_ok false when the
+// structure does not admit it (then the host factorisation runs).
+omm_status ensure_factor_maps(omm_ctx* h) {
+  if (h->fmaps_tried) return OMM_OK;
+  h->fmaps_tried = true;
+  const SppStructure& s = h->spp;
+  const SppFactorMaps mp = spp_factor_maps(s);
+  if (!mp.ok) return OMM_OK;
+  OMM_TRY(upload_vec(h, &h->d_foff, mp.foff));
+  OMM_TRY(upload_vec(h, &h->d_child0, mp.child0));
+  OMM_TRY(upload_vec(h, &h->d_child1, mp.child1));
+  OMM_TRY(upload_vec(h, &h->d_asm_ptr, mp.asm_ptr));
+  OMM_TRY(upload_vec(h, &h->d_asm_pos, mp.asm_pos));
+  OMM_TRY(upload_vec(h, &h->d_asm_src, mp.asm_src));
+  OMM_TRY(upload_vec(h, &h->d_nbr, mp.nbr));
+  OMM_TRY(upload_vec(h, &h->d_emap, mp.emap));
+  OMM_TRY(upload_vec(h, &h->d_leaf_of, mp.leaf_of));
+  OMM_TRY(upload_vec(h, &h->d_Vdbl, h->Vh));
+  OMM_TRY(h->dalloc_t(&h->d_qq, (size_t)2 * PMAX * 27 * sizeof(double2)));
+  std::vector<int> hn;
+  h->hn_start.clear();
+  h->hn_count.clear();
+  h->hn_tiles.clear();
+  for (const auto& lev : s.levels) {
+    h->hn_start.push_back((int)hn.size());
+    h->hn_count.push_back((int)lev.size());
+    int tiles = 0;
+    for (int id : lev) {
+      const int tn = (s.nodes[id].ns + 31) / 32, tb = (s.nodes[id].nb + 31) / 32;
+      tiles = std::max(tiles, 2 * tn * tb);
+    }
+    h->hn_tiles.push_back(tiles);
+    hn.insert(hn.end(), lev.begin(), lev.end());
+  }
+  OMM_TRY(upload_vec(h, &h->d_hnodes, hn));
+  OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "maps sync"));
+  h->front_size = mp.front_size;
+  h->fmaps_ok = true;
+  return OMM_OK;
+}
+
+// The multifrontal factorisation of P for the P poles of sten on the device, height by
+// height, in FP64, into the handle's factor and leaf arrays (rounded once to complex64 for
+// a mixed handle); the pivot statistics into spp_poles.  The fronts (and, for a mixed
+// handle, the FP64 factor) live in work buffers for the duration of the call.
+omm_status device_factor(omm_ctx* h, int P, const std::vector<SppStencil>& sten) {
+  const SppStructure& s = h->spp;
+  const int na = (int)s.offsets.size() / 3;
+  if (na > 27) return OMM_EUNSUPPORTED;
+  std::vector<double2> qq((size_t)2 * PMAX * 27, make_double2(0.0, 0.0));
+  for (int j = 0; j < P; ++j)
+    for (int t = 0; t < na; ++t) {
+      qq[(size_t)j * na + t] = make_double2(sten[j].q[t].real(), sten[j].q[t].imag());
+      qq[(size_t)PMAX * 27 + (size_t)j * na + t] = make_double2(sten[j].qg[t].real(), sten[j].qg[t].imag());
+    }
+  OMM_TRY(cuda_status(cudaMemcpyAsync(h->d_qq, qq.data(), qq.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st),
+                      "q"));
+  const int nn = (int)s.nodes.size();
+  const size_t fbytes = (size_t)P * h->front_size * sizeof(double2), pbytes = (size_t)P * nn * 3 * sizeof(double);
+  const size_t nfac = (size_t)P * s.factor_size, nleaf = (size_t)P * s.leaf_size;
+  const size_t wbytes = h->dbl ? 0 : (nfac + nleaf) * sizeof(double2);
+  double2* fronts = nullptr;
+  double* pst = nullptr;
+  double2* work64 = nullptr;   // mixed handles: the FP64 factor, then the FP64 leaf data
+  OMM_TRY(h->dalloc_t(&fronts, fbytes));
+  omm_status rc = h->dalloc_t(&pst, pbytes);
+  if (rc == OMM_OK && wbytes) rc = h->dalloc_t(&work64, wbytes);
+  double2* fac64 = h->dbl ? (double2*)h->factor : work64;
+  double2* leaf64 = h->dbl ? (double2*)h->leafvals : work64 + nfac;
+  if (rc == OMM_OK) {
+    FactorArgs fa;
+    fa.node_ns = h->d_node_ns;
+    fa.node_nb = h->d_node_nb;
+    fa.node_boff = h->d_node_boff;
+    fa.node_wf = h->d_node_wf;
+    fa.node_wb = h->d_node_wb;
+    fa.foff = h->d_foff;
+    fa.child0 = h->d_child0;
+    fa.child1 = h->d_child1;
+    fa.asm_ptr = h->d_asm_ptr;
+    fa.asm_pos = h->d_asm_pos;
+    fa.asm_src = h->d_asm_src;
+    fa.nbr = h->d_nbr;
+    fa.emap = h->d_emap;
+    fa.leaf_of = h->d_leaf_of;
+    fa.leaf_voff = h->d_leaf_voff;
+    fa.leaf_ioff_bs = h->d_leaf_ioff_bs;
+    fa.leaf_ioff_sb = h->d_leaf_ioff_sb;
+    fa.leaf_bs_idx = h->d_leaf_bs_idx;
+    fa.leaf_sb_idx = h->d_leaf_sb_idx;
+    fa.leaf_bw = s.leaf_bw;
+    fa.na = na;
+    fa.nnodes = nn;
+    fa.front_size = h->front_size;
+    fa.factor_size = s.factor_size;
+    fa.leaf_size = s.leaf_size;
+    fa.V = h->d_Vdbl;
+    fa.lmean = sten[0].lmean;
+    fa.q = h->d_qq;
+    fa.qg = h->d_qq + (size_t)PMAX * 27;
+    fa.pivot_floor = h->prm.pivot_floor;
+    for (size_t lh = 0; lh < s.levels.size() && rc == OMM_OK; ++lh)
+      rc = cuda_status(launch_factor_height(fa, h->d_hnodes + h->hn_start[lh], h->hn_count[lh], P, h->hn_tiles[lh],
+                                            fronts, fac64, leaf64, pst, h->st),
+                       "factor");
+    if (rc == OMM_OK && !h->dbl)
+      rc = cuda_status(launch_factor_to_c64(fac64, (float2*)h->factor, nfac, h->st), "factor c64");
+    if (rc == OMM_OK && !h->dbl && nleaf)
+      rc = cuda_status(launch_factor_to_c64(leaf64, (float2*)h->leafvals, nleaf, h->st), "leaf c64");
+    std::vector<double> ps((size_t)P * nn * 3);
+    if (rc == OMM_OK)
+      rc = cuda_status(cudaMemcpyAsync(ps.data(), pst, pbytes, cudaMemcpyDeviceToHost, h->st), "pivots");
+    if (rc == OMM_OK) rc = cuda_status(cudaStreamSynchronize(h->st), "factor sync");
+    if (rc == OMM_OK)
+      for (int j = 0; j < P; ++j) {
+        SppPole& pp = h->spp_poles[j];
+        pp.pivot_min = 1e300;
+        pp.pivot_max = 0.0;
+        pp.nperturbed = 0;
+        for (int id = 0; id < nn; ++id) {
+          const double* e = &ps[((size_t)j * nn + id) * 3];
+          pp.pivot_min = std::min(pp.pivot_min, e[0]);
+          pp.pivot_max = std::max(pp.pivot_max, e[1]);
+          pp.nperturbed += (int)e[2];
+        }
+      }
+  }
+  cudaStreamSynchronize(h->st);   // the work buffers are idle before they are released
+  h->dfree(work64, wbytes);
+  h->dfree(pst, pbytes);
+  h->dfree(fronts, fbytes);
+  return rc;
+}
+
 omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
   if (!h || !z || !w || P < 1 || P > PMAX) return OMM_EINVAL;
   for (int j = 0; j < 2 * P; ++j)
@@ -1236,19 +1394,31 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
     std::vector<cd> q_all;
     if (inner == OMM_INNER_SPARSIFY) {
       OMM_TRY(build_spp(h));
+      if (h->prm.device_factor) OMM_TRY(ensure_factor_maps(h));
+      const bool dev = h->prm.device_factor && h->fmaps_ok;
       h->spp_poles.assign(P, SppPole());
       std::vector<std::vector<cd>> gh(P);
+      std::vector<SppStencil> sten(P);
       // one thread per pole; host cores beyond the poles factor each pole's elimination tree
-      // with up to 4 threads (the factor is the same bitwise)
+      // with up to 4 threads (the factor is the same bitwise).  With the device
+      // factorisation the host computes only each pole's stencil data (q by the SVD).
       const int hw = std::max(1, (int)std::thread::hardware_concurrency());
       const int nth = std::max(1, std::min<int>(P, hw));
       const int tpp = std::max(1, std::min(4, hw / nth));
       std::vector<std::thread> th;
       for (int t = 0; t < nth; ++t)
         th.emplace_back([&, t]() {
-          for (int j = t; j < P; j += nth)
-            spp_setup_pole(h->spp, h->kin, h->Vh.data(), h->shift, cd(z[2 * j], z[2 * j + 1]), h->prm.pivot_floor,
-                           h->spp_poles[j], gh[j], tpp);
+          for (int j = t; j < P; j += nth) {
+            if (dev) {
+              spp_pole_stencil(h->spp, h->kin, h->Vh.data(), h->shift, cd(z[2 * j], z[2 * j + 1]), sten[j], gh[j]);
+              h->spp_poles[j].q = sten[j].q;
+              h->spp_poles[j].sigma_min = sten[j].sigma_min;
+              h->spp_poles[j].sigma_max = sten[j].sigma_max;
+            } else {
+              spp_setup_pole(h->spp, h->kin, h->Vh.data(), h->shift, cd(z[2 * j], z[2 * j + 1]), h->prm.pivot_floor,
+                             h->spp_poles[j], gh[j], tpp);
+            }
+          }
         });
       for (auto& t : th) t.join();
       h->nq = (int)h->spp.offsets.size() / 3;
@@ -1270,14 +1440,20 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
         OMM_TRY(cuda_status(cudaMemsetAsync(h->xnd, 0, (size_t)P * h->N * n * h->csz, h->st), "memset"));
         h->Pfac = P;
       }
-      std::vector<cd> fall((size_t)P * fs);
-      for (int j = 0; j < P; ++j) std::copy(h->spp_poles[j].factor.begin(), h->spp_poles[j].factor.end(), fall.begin() + (size_t)j * fs);
-      OMM_TRY(upload_complex(h, h->factor, fall, h->dbl));
-      const long long ls = h->spp.leaf_size;
-      std::vector<cd> lall((size_t)P * ls);
-      for (int j = 0; j < P; ++j)
-        std::copy(h->spp_poles[j].leafval.begin(), h->spp_poles[j].leafval.end(), lall.begin() + (size_t)j * ls);
-      OMM_TRY(upload_complex(h, h->leafvals, lall, h->dbl));
+      h->last_factor_device = dev;
+      if (dev) {
+        OMM_TRY(device_factor(h, P, sten));
+      } else {
+        std::vector<cd> fall((size_t)P * fs);
+        for (int j = 0; j < P; ++j)
+          std::copy(h->spp_poles[j].factor.begin(), h->spp_poles[j].factor.end(), fall.begin() + (size_t)j * fs);
+        OMM_TRY(upload_complex(h, h->factor, fall, h->dbl));
+        const long long ls = h->spp.leaf_size;
+        std::vector<cd> lall((size_t)P * ls);
+        for (int j = 0; j < P; ++j)
+          std::copy(h->spp_poles[j].leafval.begin(), h->spp_poles[j].leafval.end(), lall.begin() + (size_t)j * ls);
+        OMM_TRY(upload_complex(h, h->leafvals, lall, h->dbl));
+      }
     } else {
       std::vector<cd> gh;
       for (int j = 0; j < P; ++j) {
@@ -1512,7 +1688,7 @@ omm_status omm_precond_apply(omm_t h, int pole, const void* B, void* U, int ncol
   TrsvLevels lv = trsv_levels(h);
   const void* f = (char*)h->factor + (size_t)pole * h->spp.factor_size * h->csz;
   OMM_TRY(cuda_status(launch_spp_solve(SPP_ALL, h->dbl, a, lv, leaf_args(h, pole), 1, h->tv, h->ynd, h->ubuf, U, h->xnd,
-                                       f, nullptr, h->trsv_smem, h->st),
+                                       f, nullptr, h->trsv_smem, h->prm.launch_overlap, h->st),
                       "spp"));
   return cuda_status(cudaStreamSynchronize(h->st), "sync");
 }

@@ -52,6 +52,32 @@ template <typename Cd, typename Cs> __host__ __device__ __forceinline__ Cd ccast
 // ceiling only, the launch's dynamic size still sets the occupancy.
 cudaError_t raise_smem_limit(const void* func);
 
+// Programmatic dependent launch.  A kernel launched with `overlap` set may be scheduled
+// while the kernel before it on the stream is still running.  griddep_wait() returns once
+// that kernel has completed and its writes are visible (at once for an ordinary launch);
+// griddep_launch() lets the next such kernel be scheduled.  Before griddep_wait() a kernel
+// only reads data that nothing in the chain writes (factor values, index lists) and writes
+// nothing; it calls griddep_launch() after the wait, so at most two kernels of a chain are
+// resident at a time and the second one only runs its prologue early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool overlap, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 }  // namespace omm
 
 #define OMM_CUDA_TRY(expr)                                              \

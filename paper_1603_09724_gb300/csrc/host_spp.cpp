@@ -476,12 +476,13 @@ void green_symbol(int dim, int m, double kin, double lmean, double shift, cd z, 
   }
 }
 
-void spp_setup_pole(const SppStructure& st, double kin, const double* V, double shift, cd z, double pivot_floor,
-                    SppPole& out, std::vector<cd>& ghat, int threads) {
+void spp_pole_stencil(const SppStructure& st, double kin, const double* V, double shift, cd z, SppStencil& out,
+                      std::vector<cd>& ghat) {
   const int dim = st.dim, m = st.m, n = st.n;
   double lmean = 0.0;
   for (int i = 0; i < n; ++i) lmean += V[i];
   lmean /= n;
+  out.lmean = lmean;
   green_symbol(dim, m, kin, lmean, shift, z, ghat);
   std::vector<cd> g(ghat);
   idft_separable(dim, m, g);   // g[x] = G(x, 0)
@@ -529,11 +530,33 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
   out.q.resize(na);
   for (int i = 0; i < na; ++i) out.q[i] = std::conj(Vj[(size_t)jmin * na + i]);
   // (qG)(0, a_j) = sum_i q_i G(o_i, o_j) = sum_i q_i g[o_i - o_j]
-  std::vector<cd> qg(na, cd(0.0, 0.0));
+  out.qg.assign(na, cd(0.0, 0.0));
   for (int j = 0; j < na; ++j)
     for (int i = 0; i < na; ++i)
-      qg[j] += out.q[i] * g[off_flat(st.offsets[3 * i] - st.offsets[3 * j], st.offsets[3 * i + 1] - st.offsets[3 * j + 1],
-                                     st.offsets[3 * i + 2] - st.offsets[3 * j + 2])];
+      out.qg[j] += out.q[i] * g[off_flat(st.offsets[3 * i] - st.offsets[3 * j],
+                                         st.offsets[3 * i + 1] - st.offsets[3 * j + 1],
+                                         st.offsets[3 * i + 2] - st.offsets[3 * j + 2])];
+}
+
+void spp_setup_pole(const SppStructure& st, double kin, const double* V, double shift, cd z, double pivot_floor,
+                    SppPole& out, std::vector<cd>& ghat, int threads) {
+  const int dim = st.dim, m = st.m, n = st.n;
+  SppStencil sten;
+  spp_pole_stencil(st, kin, V, shift, z, sten, ghat);
+  out.q = sten.q;
+  out.sigma_min = sten.sigma_min;
+  out.sigma_max = sten.sigma_max;
+  const std::vector<cd>& qg = sten.qg;
+  const double lmean = sten.lmean;
+  const int na = (int)st.offsets.size() / 3;
+  auto off_flat = [&](int dx, int dy, int dz) {
+    return wrap(dx, m) + m * (wrap(dy, m) + (dim == 3 ? m * wrap(dz, m) : 0));
+  };
+  auto coord = [&](int p, int& x, int& y, int& zc) {
+    x = p % m;
+    y = (p / m) % m;
+    zc = dim == 3 ? p / (m * m) : 0;
+  };
   // P(row j, stencil t) = q_t + qg_t (V_{j+o_t} - l)
   auto neighbor = [&](int p, int t) {
     int x, y, zc;
@@ -711,6 +734,94 @@ void spp_setup_pole(const SppStructure& st, double kin, const double* V, double 
     out.pivot_max = std::max(out.pivot_max, ps.pmax);
     out.nperturbed += ps.nperturbed;
   }
+}
+
+SppFactorMaps spp_factor_maps(const SppStructure& st) {
+  SppFactorMaps mp;
+  const int dim = st.dim, m = st.m, n = st.n;
+  const int na = (int)st.offsets.size() / 3;
+  const int nn = (int)st.nodes.size();
+  auto off_flat = [&](int dx, int dy, int dz) {
+    return wrap(dx, m) + m * (wrap(dy, m) + (dim == 3 ? m * wrap(dz, m) : 0));
+  };
+  auto coord = [&](int p, int& x, int& y, int& zc) {
+    x = p % m;
+    y = (p / m) % m;
+    zc = dim == 3 ? p / (m * m) : 0;
+  };
+  mp.nbr.resize((size_t)n * na);
+  for (int p = 0; p < n; ++p) {
+    int x, y, zc;
+    coord(p, x, y, zc);
+    for (int t = 0; t < na; ++t)
+      mp.nbr[(size_t)p * na + t] =
+          off_flat(x + st.offsets[3 * t], y + st.offsets[3 * t + 1], zc + st.offsets[3 * t + 2]);
+  }
+  mp.foff.resize(nn);
+  mp.child0.assign(nn, -1);
+  mp.child1.assign(nn, -1);
+  mp.leaf_of.assign(nn, -1);
+  for (int i = 0; i < nn; ++i) {
+    mp.foff[i] = mp.front_size;
+    const long long nf = st.nodes[i].ns + st.nodes[i].nb;
+    mp.front_size += nf * nf;
+    const int par = st.nodes[i].parent;
+    if (par >= 0) {
+      if (mp.child0[par] < 0) mp.child0[par] = i;
+      else if (mp.child1[par] < 0) mp.child1[par] = i;
+      else return mp;   // more than two children: not a bisection tree
+    }
+  }
+  for (size_t li = 0; li < st.leaf_nodes.size(); ++li) mp.leaf_of[st.leaf_nodes[li]] = (int)li;
+  // P's entries of each front (the row and column couplings of its own unknowns, as the
+  // host factorisation assembles them), and the place of each boundary unknown in the
+  // parent's front
+  std::vector<int> loc(n, -1);
+  mp.emap.assign(st.bnd.size(), -1);
+  mp.asm_ptr.assign(nn + 1, 0);
+  std::vector<int> seen;
+  for (int s = 0; s < nn; ++s) {
+    const SppNode& nd = st.nodes[s];
+    const int ns = nd.ns, nb = nd.nb, nf = ns + nb;
+    for (int i = 0; i < ns; ++i) loc[nd.off + i] = i;
+    for (int j = 0; j < nb; ++j) loc[st.bnd[nd.boff + j]] = ns + j;
+    const size_t first = mp.asm_pos.size();
+    for (int i = 0; i < ns; ++i) {
+      const int nat = st.perm[nd.off + i];
+      int x, y, zc;
+      coord(nat, x, y, zc);
+      for (int t = 0; t < na; ++t) {
+        const int jn = st.iperm[mp.nbr[(size_t)nat * na + t]];
+        if (loc[jn] >= 0) {
+          mp.asm_pos.push_back(i * nf + loc[jn]);
+          mp.asm_src.push_back(nat * na + t);
+        }
+        const int rnat = off_flat(x - st.offsets[3 * t], y - st.offsets[3 * t + 1], zc - st.offsets[3 * t + 2]);
+        const int jr = st.iperm[rnat];
+        if (loc[jr] >= ns) {
+          mp.asm_pos.push_back(loc[jr] * nf + i);
+          mp.asm_src.push_back(rnat * na + t);
+        }
+      }
+    }
+    seen.assign(mp.asm_pos.begin() + first, mp.asm_pos.end());
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return mp;   // two entries on one position
+    mp.asm_ptr[s + 1] = (int)mp.asm_pos.size();
+    for (int c : {mp.child0[s], mp.child1[s]}) {
+      if (c < 0) continue;
+      const SppNode& cn = st.nodes[c];
+      for (int a = 0; a < cn.nb; ++a) mp.emap[cn.boff + a] = loc[st.bnd[cn.boff + a]];
+    }
+    for (int i = 0; i < ns; ++i) loc[nd.off + i] = -1;
+    for (int j = 0; j < nb; ++j) loc[st.bnd[nd.boff + j]] = -1;
+  }
+  for (int s = 0; s < nn; ++s)
+    if (st.nodes[s].parent >= 0)
+      for (int a = 0; a < st.nodes[s].nb; ++a)
+        if (mp.emap[st.nodes[s].boff + a] < 0) return mp;   // a boundary unknown missing from the parent's front
+  mp.ok = true;
+  return mp;
 }
 
 }  // namespace omm

@@ -96,6 +96,8 @@ template <typename T>
 __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const int* __restrict__ lunk, int cnt,
                                                               size_t nsys, const cx_t<T>* __restrict__ b,
                                                               const cx_t<T>* u, cx_t<T>* x, const int* __restrict__ active) {
+  griddep_wait();
+  griddep_launch();
   assemble_tile<T>(a, lunk, cnt, nsys, b, u, x, active, blockIdx.x, blockIdx.y);
 }
 
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(AS_I * 32) assemble_kernel(TrsvArgs a, const i
 // RBV rows x RTV right-hand sides per CTA with NTH threads, 4 rows x TC columns per thread.
 // The host's row blocks are 64 rows; a smaller RBV splits each into `split` CTAs (grid.y):
 // for the top of the tree, where 64-row blocks leave most SMs idle, and for thin nodes.
-template <typename T, bool FWD, int RBV, int RTV, int NTH>
+template <typename T, bool FWD, int RBV, int RTV, int NTH, bool GD = false>
 __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restrict__ blocks, cx_t<T>* ynd, cx_t<T>* u,
                                           cx_t<T>* x, cx_t<T>* xnd, const cx_t<T>* __restrict__ factor,
                                           const int* __restrict__ active, int split, int bx, int by, int bz,
@@ -126,6 +128,25 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
   if (r0 >= M) return;   // a split past the node's last row (uniform over the CTA)
   const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
+  // W tiles: each thread holds WPT elements of the next tile in registers while the
+  // current tile is consumed from shared memory (one barrier per k step).  The first tile
+  // is loaded before the wait on the previous launch (GD): the factor is not written there.
+  constexpr int WPT = RBV * KT / NTH;
+  C wreg[WPT];
+  auto load_w = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < WPT; ++q) {
+      const int idx = tid + q * NTH;
+      const int kk = idx % KT, rr = idx / KT;   // k fastest: coalesced rows of W
+      const int r = r0 + rr, k = k0 + kk;
+      wreg[q] = (r < M && k < K) ? W[(size_t)r * K + k] : mk<C>(0, 0);
+    }
+  };
+  load_w(0);
+  if (GD) {
+    griddep_wait();
+    griddep_launch();
+  }
   // ---- right-hand-side block, i fastest (contiguous runs of one system's column); FB
   // independent loads in flight per thread
   constexpr int FB = 8;
@@ -161,20 +182,6 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < TC; ++j) acc[i][j] = mk<C>(0, 0);
-  // W tiles: each thread holds WPT elements of the next tile in registers while the
-  // current tile is consumed from shared memory (one barrier per k step)
-  constexpr int WPT = RBV * KT / NTH;
-  C wreg[WPT];
-  auto load_w = [&](int k0) {
-#pragma unroll
-    for (int q = 0; q < WPT; ++q) {
-      const int idx = tid + q * NTH;
-      const int kk = idx % KT, rr = idx / KT;   // k fastest: coalesced rows of W
-      const int r = r0 + rr, k = k0 + kk;
-      wreg[q] = (r < M && k < K) ? W[(size_t)r * K + k] : mk<C>(0, 0);
-    }
-  };
-  load_w(0);
   int buf = 0;
   for (int k0 = 0; k0 < K; k0 += KT, buf ^= 1) {
 #pragma unroll
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(NTH) trsv_gemm_kernel(TrsvArgs a, const int* _
                                                         const cx_t<T>* __restrict__ factor,
                                                         const int* __restrict__ active, int split) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  gemm_tile<T, FWD, RBV, RTV, NTH>(a, blocks, ynd, u, x, xnd, factor, active, split, blockIdx.x, blockIdx.y,
+  gemm_tile<T, FWD, RBV, RTV, NTH, true>(a, blocks, ynd, u, x, xnd, factor, active, split, blockIdx.x, blockIdx.y,
                                    blockIdx.z, smem_raw);
 }
 
@@ -262,7 +269,7 @@ size_t sk_smem_bytes(int K) {
   return (bs + (size_t)KS * SK_WK * (RBS + 1)) * cs;
 }
 
-template <typename T, bool FWD, int KS, int RBS>
+template <typename T, bool FWD, int KS, int RBS, bool GD = false>
 __device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __restrict__ blocks, cx_t<T>* ynd,
                                              cx_t<T>* u, cx_t<T>* x, cx_t<T>* xnd, const cx_t<T>* __restrict__ factor,
                                              const int* __restrict__ active, int split, int bx, int by, int bz,
@@ -285,6 +292,29 @@ __device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __res
   C* Wall = Bs + bs_elems;                                                   // [KS][WK][RBS + 1]
   const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
+  // ---- this warp's slice of K; its first W chunk is loaded before the wait on the
+  // previous launch (GD): the factor is not written there
+  const int w = tid >> 5, lane = tid & 31;
+  const int rg = lane / CGS, cg = lane % CGS;
+  const int kw = (K + KS - 1) / KS;
+  const int kb = w * kw, ke = min(K, kb + kw);
+  C* Ws = Wall + (size_t)w * SK_WK * (RBS + 1);
+  constexpr int WPL = RBS * SK_WK / 32;   // W values per lane per chunk
+  C wv[WPL];
+  auto load_w = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+      const int idx = lane + 32 * q;
+      const int kk = idx % SK_WK, rr = idx / SK_WK;   // k fastest: runs of one W row
+      const int r = r0 + rr, k = k0 + kk;
+      wv[q] = (r < M && k < ke) ? W[(size_t)r * K + k] : mk<C>(0, 0);
+    }
+  };
+  if (kb < ke) load_w(kb);
+  if (GD) {
+    griddep_wait();
+    griddep_launch();
+  }
   // ---- right-hand-side block (i fastest: contiguous runs of one system's column)
   constexpr int FB = 8;
   const int boff = a.node_boff[node];
@@ -312,29 +342,11 @@ __device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __res
     }
   }
   __syncthreads();
-  // ---- this warp's slice of K
-  const int w = tid >> 5, lane = tid & 31;
-  const int rg = lane / CGS, cg = lane % CGS;
-  const int kw = (K + KS - 1) / KS;
-  const int kb = w * kw, ke = min(K, kb + kw);
-  C* Ws = Wall + (size_t)w * SK_WK * (RBS + 1);
   C acc[4][TCS];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < TCS; ++j) acc[i][j] = mk<C>(0, 0);
-  constexpr int WPL = RBS * SK_WK / 32;   // W values per lane per chunk
-  C wv[WPL];
-  auto load_w = [&](int k0) {
-#pragma unroll
-    for (int q = 0; q < WPL; ++q) {
-      const int idx = lane + 32 * q;
-      const int kk = idx % SK_WK, rr = idx / SK_WK;   // k fastest: runs of one W row
-      const int r = r0 + rr, k = k0 + kk;
-      wv[q] = (r < M && k < ke) ? W[(size_t)r * K + k] : mk<C>(0, 0);
-    }
-  };
-  if (kb < ke) load_w(kb);
   for (int k0 = kb; k0 < ke; k0 += SK_WK) {
     __syncwarp();   // the previous chunk has been read
 #pragma unroll
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(32 * KS) trsv_gemm_sk_kernel(TrsvArgs a, const
                                                                const cx_t<T>* __restrict__ factor,
                                                                const int* __restrict__ active, int split) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  gemm_sk_tile<T, FWD, KS, RBS>(a, blocks, ynd, u, x, xnd, factor, active, split, blockIdx.x, blockIdx.y, blockIdx.z,
+  gemm_sk_tile<T, FWD, KS, RBS, true>(a, blocks, ynd, u, x, xnd, factor, active, split, blockIdx.x, blockIdx.y, blockIdx.z,
                                 smem_raw);
 }
 
@@ -499,11 +511,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
   int* ibnd = iperm + ns;           // ND index of halo unknown j
   int* ibs = ibnd + nb;            // F_BS columns (leaf unknowns) per halo row, -1 padded
   int* isb = ibs + nb * LNB;        // F_SB columns (halo unknowns) per leaf row, -1 padded
-  {
-    const int c = c0 + tid;
-    live[tid] = (c < a.N) && (!active || active[(size_t)p * a.N + c]);
-  }
-  {
+  {   // the leaf's factor values and index lists (not written by the kernels before this one)
     const C* v = reinterpret_cast<const C*>(la.vals) + (size_t)p * la.leaf_size + la.voff[li];
     const int nv = (int)leaf_vals_count(ns, nb, bw);
     for (int e = tid; e < nv; e += LT) vs[e] = v[e];
@@ -518,6 +526,12 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
       for (int e = tid; e < ns * LNB; e += LT) isb[e] = sbi[e];
     }
   }
+  griddep_wait();
+  griddep_launch();
+  {
+    const int c = c0 + tid;
+    live[tid] = (c < a.N) && (!active || active[(size_t)p * a.N + c]);
+  }
   __syncthreads();
   const C* Lb = vs;
   const C* Ub = Lb + ns * bw;
@@ -526,29 +540,43 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
   const size_t s0 = (size_t)p * a.N + c0;
   C* y = ys + tid;
   const bool mine = live[tid];
+  // Column passes between global memory and ys: warp wq takes the columns wq, wq + NWQ,
+  // ... and its lanes consecutive leaf unknowns (i0 + lane, i0 + lane + 32), so that a
+  // warp's accesses are contiguous runs of one column and no index needs a division.
+  const int lane = tid & 31, wq = tid >> 5;
+  constexpr int NWQ = LT / 32;
+  static_assert(LT % (NWQ * LGB) == 0, "column batches tile the CTA");
   if (FWD) {
-    for (int base = tid; base < ns * LT; base += LGB * LT) {   // LGB independent loads in flight
-      C v[LGB];
+    for (int i0 = 0; i0 < ns; i0 += 64)
+      for (int cb = wq; cb < LT; cb += NWQ * LGB) {   // 2 x LGB independent loads in flight
+        C v[LGB][2];
 #pragma unroll
-      for (int q = 0; q < LGB; ++q) {
-        const int idx = base + q * LT;
-        const int i = idx % ns, cc = idx / ns;
-        if (idx < ns * LT && live[cc]) v[q] = b[(s0 + cc) * a.n + off + i];
-      }
+        for (int q = 0; q < LGB; ++q)
 #pragma unroll
-      for (int q = 0; q < LGB; ++q) {
-        const int idx = base + q * LT;
-        const int i = idx % ns, cc = idx / ns;
-        if (idx < ns * LT && live[cc]) ys[i * LDY + cc] = v[q];
+          for (int h = 0; h < 2; ++h) {
+            const int cc = cb + q * NWQ, i = i0 + lane + 32 * h;
+            if (i < ns && live[cc]) v[q][h] = b[(s0 + cc) * a.n + off + i];
+          }
+#pragma unroll
+        for (int q = 0; q < LGB; ++q)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cc = cb + q * NWQ, i = i0 + lane + 32 * h;
+            if (i < ns && live[cc]) ys[i * LDY + cc] = v[q][h];
+          }
       }
-    }
     __syncthreads();
     if (mine) band_lower<T>(y, ns, bw, Lb);
     __syncthreads();
-    for (int idx = tid; idx < ns * LT; idx += LT) {
-      const int i = idx % ns, cc = idx / ns;
-      if (live[cc]) ynd[(s0 + cc) * a.n + off + i] = ys[i * LDY + cc];
-    }
+    for (int i0 = 0; i0 < ns; i0 += 64)
+      for (int cc = wq; cc < LT; cc += NWQ) {
+        if (!live[cc]) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = i0 + lane + 32 * h;
+          if (i < ns) ynd[(s0 + cc) * a.n + off + i] = ys[i * LDY + cc];
+        }
+      }
     __syncthreads();
     if (!mine) return;
     band_upper<T>(y, ns, bw, Ub);
@@ -563,54 +591,68 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
       u[(size_t)(uoff + j) * a.S + s0 + tid] = acc;
     }
   } else {
-    for (int base = tid; base < ns * LT; base += 4 * LT) {
-      C acc[4];
+    // F_SB x_B: each lane's row (its couplings and halo positions read once) for 4 columns
+    constexpr int HQ = 4;
+    for (int i0 = 0; i0 < ns; i0 += 64)
+      for (int cb = wq; cb < LT; cb += NWQ * HQ)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int idx = base + q * LT;
-        const int i = idx % ns, cc = idx / ns;
-        acc[q] = mk<C>(0, 0);
-        if (idx < ns * LT && live[cc]) {
-          const C* xs = xnd + (s0 + cc) * a.n;
+        for (int h = 0; h < 2; ++h) {
+          const int i = i0 + lane + 32 * h;
+          if (i >= ns) continue;
+          C acc[HQ];
+          bool on[HQ];
+#pragma unroll
+          for (int q = 0; q < HQ; ++q) {
+            acc[q] = mk<C>(0, 0);
+            on[q] = live[cb + q * NWQ];
+          }
 #pragma unroll
           for (int t = 0; t < LNB; ++t) {   // -1 entries trail: same order as a breaking loop
             const int j = isb[i * LNB + t];
-            if (j >= 0) acc[q] = cfma(Fsb[i * LNB + t], xs[ibnd[j]], acc[q]);
-          }
-        }
-      }
+            if (j < 0) continue;
+            const C f = Fsb[i * LNB + t];
+            const int bj = ibnd[j];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int idx = base + q * LT;
-        const int i = idx % ns, cc = idx / ns;
-        if (idx < ns * LT && live[cc]) ys[i * LDY + cc] = acc[q];
-      }
-    }
+            for (int q = 0; q < HQ; ++q)
+              if (on[q]) acc[q] = cfma(f, xnd[(s0 + cb + q * NWQ) * a.n + bj], acc[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < HQ; ++q)
+            if (on[q]) ys[i * LDY + cb + q * NWQ] = acc[q];
+        }
     __syncthreads();
     if (mine) band_lower<T>(y, ns, bw, Lb);
     __syncthreads();
-    for (int base = tid; base < ns * LT; base += LGB * LT) {
-      C v[LGB];
+    for (int i0 = 0; i0 < ns; i0 += 64)
+      for (int cb = wq; cb < LT; cb += NWQ * LGB) {
+        C v[LGB][2];
 #pragma unroll
-      for (int q = 0; q < LGB; ++q) {
-        const int idx = base + q * LT;
-        const int i = idx % ns, cc = idx / ns;
-        if (idx < ns * LT && live[cc]) v[q] = ynd[(s0 + cc) * a.n + off + i];
-      }
+        for (int q = 0; q < LGB; ++q)
 #pragma unroll
-      for (int q = 0; q < LGB; ++q) {
-        const int idx = base + q * LT;
-        const int i = idx % ns, cc = idx / ns;
-        if (idx < ns * LT && live[cc]) ys[i * LDY + cc] = csub(v[q], ys[i * LDY + cc]);
+          for (int h = 0; h < 2; ++h) {
+            const int cc = cb + q * NWQ, i = i0 + lane + 32 * h;
+            if (i < ns && live[cc]) v[q][h] = ynd[(s0 + cc) * a.n + off + i];
+          }
+#pragma unroll
+        for (int q = 0; q < LGB; ++q)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cc = cb + q * NWQ, i = i0 + lane + 32 * h;
+            if (i < ns && live[cc]) ys[i * LDY + cc] = csub(v[q][h], ys[i * LDY + cc]);
+          }
       }
-    }
     __syncthreads();
     if (mine) band_upper<T>(y, ns, bw, Ub);
     __syncthreads();
-    for (int idx = tid; idx < ns * LT; idx += LT) {
-      const int i = idx % ns, cc = idx / ns;
-      if (live[cc]) x[(s0 + cc) * a.n + iperm[i]] = ys[i * LDY + cc];
-    }
+    for (int i0 = 0; i0 < ns; i0 += 64)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + lane + 32 * h;
+        if (i >= ns) continue;
+        const int xi = iperm[i];
+        for (int cc = wq; cc < LT; cc += NWQ)
+          if (live[cc]) x[(s0 + cc) * a.n + xi] = ys[i * LDY + cc];
+      }
   }
 }
 
@@ -625,7 +667,7 @@ size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb) {
 template <typename T, bool FWD, int RBV, int RTV, int NTH>
 static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
                                 const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
-                                const int* active, cudaStream_t st) {
+                                const int* active, bool ov, cudaStream_t st) {
   using C = cx_t<T>;
   auto k = trsv_gemm_kernel<T, FWD, RBV, RTV, NTH>;
   cudaError_t e = raise_smem_limit((const void*)k);
@@ -635,8 +677,8 @@ static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count,
   const dim3 grid((a.N + RTV - 1) / RTV, count * split, P);
   const size_t sm = std::max((size_t)kmax * RTV, (size_t)RBV * (RTV + 1)) * sizeof(C);
   (void)b;
-  k<<<grid, NTH, sm, st>>>(a, blocks, (C*)ynd, (C*)u, (C*)x, (C*)xnd, (const C*)factor, active, split);
-  return cudaGetLastError();
+  return launch_k(ov, k, grid, dim3(NTH), sm, st, a, blocks, (C*)ynd, (C*)u, (C*)x, (C*)xnd, (const C*)factor, active,
+                  split);
 }
 
 // Tile choice per level from its largest row count mmax (M = ns + nb forward, ns backward)
@@ -645,16 +687,15 @@ static cudaError_t launch_level(const TrsvArgs& a, const int* blocks, int count,
 template <typename T, bool FWD, int KS, int RBS>
 static cudaError_t launch_level_sk(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
                                    void* ynd, void* u, void* x, void* xnd, const void* factor, const int* active,
-                                   cudaStream_t st) {
+                                   bool ov, cudaStream_t st) {
   using C = cx_t<T>;
   auto k = trsv_gemm_sk_kernel<T, FWD, KS, RBS>;
   cudaError_t e = raise_smem_limit((const void*)k);
   if (e != cudaSuccess) return e;
   const int split = (std::min(RB, mmax) + RBS - 1) / RBS;   // RBS-row CTAs per 64-row host block
   const dim3 grid((a.N + SK_RT - 1) / SK_RT, count * split, P);
-  k<<<grid, 32 * KS, sk_smem_bytes<T, KS, RBS>(kmax), st>>>(a, blocks, (C*)ynd, (C*)u, (C*)x, (C*)xnd,
-                                                            (const C*)factor, active, split);
-  return cudaGetLastError();
+  return launch_k(ov, k, grid, dim3(32 * KS), sk_smem_bytes<T, KS, RBS>(kmax), st, a, blocks, (C*)ynd, (C*)u,
+                  (C*)x, (C*)xnd, (const C*)factor, active, split);
 }
 
 // Split-K launch for a level whose grid is small and whose inner dimension is long:
@@ -662,7 +703,7 @@ static cudaError_t launch_level_sk(const TrsvArgs& a, const int* blocks, int cou
 template <typename T, bool FWD>
 static bool try_level_sk(cudaError_t* err, const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax,
                          int P, void* ynd, void* u, void* x, void* xnd, const void* factor, const int* active,
-                         cudaStream_t st) {
+                         bool ov, cudaStream_t st) {
   if (kmax < 48) return false;
   const int KS = kmax >= 128 ? 8 : 4;
   const int RBS = mmax <= 16 ? 16 : 32;
@@ -670,41 +711,41 @@ static bool try_level_sk(cudaError_t* err, const TrsvArgs& a, const int* blocks,
                             : (RBS == 16 ? sk_smem_bytes<T, 4, 16>(kmax) : sk_smem_bytes<T, 4, 32>(kmax));
   if (sm > 200 * 1024) return false;
   if (KS == 8 && RBS == 16)
-    *err = launch_level_sk<T, FWD, 8, 16>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+    *err = launch_level_sk<T, FWD, 8, 16>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, ov, st);
   else if (KS == 8)
-    *err = launch_level_sk<T, FWD, 8, 32>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+    *err = launch_level_sk<T, FWD, 8, 32>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, ov, st);
   else if (RBS == 16)
-    *err = launch_level_sk<T, FWD, 4, 16>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+    *err = launch_level_sk<T, FWD, 4, 16>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, ov, st);
   else
-    *err = launch_level_sk<T, FWD, 4, 32>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, st);
+    *err = launch_level_sk<T, FWD, 4, 32>(a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor, active, ov, st);
   return true;
 }
 
 template <typename T, bool FWD>
 static cudaError_t run_level(const TrsvArgs& a, const int* blocks, int count, int kmax, int mmax, int P,
                              const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
-                             const int* active, cudaStream_t st) {
+                             const int* active, bool ov, cudaStream_t st) {
   constexpr int RT = TrsvCfg<T>::RT;
   {
     // grids that leave most SMs idle with the tiled kernel: split K across warps instead
     const long tiled = (long)count * ((a.N + RT - 1) / RT) * P * ((std::min(RB, mmax) + 31) / 32);
     cudaError_t e = cudaSuccess;
     if (tiled < 4 * 152 && try_level_sk<T, FWD>(&e, a, blocks, count, kmax, mmax, P, ynd, u, x, xnd, factor,
-                                                 active, st))
+                                                 active, ov, st))
       return e;
   }
   if (mmax <= 16)
-    return launch_level<T, FWD, 16, RT, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
+    return launch_level<T, FWD, 16, RT, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, ov, st);
   const long ctas = (long)count * ((a.N + RT - 1) / RT) * P;
   if (ctas >= 8 * 152 && mmax > 32)
-    return launch_level<T, FWD, 64, RT, 128>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
-  return launch_level<T, FWD, 32, RT / 2, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, st);
+    return launch_level<T, FWD, 64, RT, 128>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, ov, st);
+  return launch_level<T, FWD, 32, RT / 2, 64>(a, blocks, count, kmax, mmax, P, b, ynd, u, x, xnd, factor, active, ov, st);
 }
 
 template <typename T>
 static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
                          const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
-                         const int* active, size_t smem_total, cudaStream_t st) {
+                         const int* active, size_t smem_total, bool ov, cudaStream_t st) {
   using C = cx_t<T>;
   (void)smem_total;
   auto leaf_f = leaf_kernel<T, true>;
@@ -718,29 +759,33 @@ static cudaError_t run_t(int phases, const TrsvArgs& a, const TrsvLevels& lv, co
   const size_t lsm = leaf_smem_bytes<T>(la.max_ns, la.max_nb, la.bw);
   const dim3 lgrid((a.N + LT - 1) / LT, la.nleaves, P);
   if (leaves && (phases & SPP_LEAF_FWD)) {
-    leaf_f<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)xnd, active);
+    cudaError_t e = launch_k(ov, leaf_f, lgrid, dim3(LT), lsm, st, a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x,
+                             (const C*)xnd, active);
+    if (e != cudaSuccess) return e;
   }
   for (int h = leaves ? 1 : 0; h < lv.nlevels && (phases & SPP_LEVELS_FWD); ++h) {
     if (lv.fcount[h] == 0) continue;
     if (lv.ucount[h] > 0) {
       const size_t nsys = (size_t)P * a.N;   // systems of this launch (a.S is the row stride of u)
       const dim3 agrid((lv.ucount[h] + AS_I - 1) / AS_I, (unsigned)((nsys + 31) / 32));
-      assemble_kernel<T><<<agrid, AS_I * 32, 0, st>>>(a, lv.lunk + lv.ustart[h], lv.ucount[h], nsys, (const C*)b,
-                                                       (const C*)u, (C*)xnd, active);
+      cudaError_t e = launch_k(ov, assemble_kernel<T>, agrid, dim3(AS_I * 32), 0, st, a, lv.lunk + lv.ustart[h],
+                               lv.ucount[h], nsys, (const C*)b, (const C*)u, (C*)xnd, active);
+      if (e != cudaSuccess) return e;
     }
     cudaError_t e = run_level<T, true>(a, lv.fblocks + 2 * lv.fstart[h], lv.fcount[h], lv.fkmax[h], lv.bkmax[h], P,
-                                       b, ynd, u, x, xnd, factor, active, st);
+                                       b, ynd, u, x, xnd, factor, active, ov, st);
     if (e != cudaSuccess) return e;
   }
   for (int h = lv.nlevels - 1; h >= (leaves ? 1 : 0) && (phases & SPP_LEVELS_BWD); --h) {
     if (lv.bcount[h] == 0) continue;
     cudaError_t e = run_level<T, false>(a, lv.bblocks + 2 * lv.bstart[h], lv.bcount[h], lv.bkmax[h], lv.fkmax[h], P,
-                                        b, ynd, u, x, xnd, factor, active, st);
+                                        b, ynd, u, x, xnd, factor, active, ov, st);
     if (e != cudaSuccess) return e;
   }
   if (leaves && (phases & SPP_LEAF_BWD))
-    leaf_b<<<lgrid, LT, lsm, st>>>(a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)xnd, active);
-  return cudaGetLastError();
+    return launch_k(ov, leaf_b, lgrid, dim3(LT), lsm, st, a, la, (const C*)b, (C*)ynd, (C*)u, (C*)x, (const C*)xnd,
+                    active);
+  return cudaSuccess;
 }
 
 // ---- all supernode heights of one application in one cooperative launch
@@ -958,9 +1003,9 @@ cudaError_t launch_spp_levels_persistent(bool dbl, const TrsvArgs& a, const Trsv
 
 cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
                              const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
-                             const int* active, size_t smem, cudaStream_t st) {
-  if (dbl) return run_t<double>(phases, a, lv, la, P, b, ynd, u, x, xnd, factor, active, smem, st);
-  return run_t<float>(phases, a, lv, la, P, b, ynd, u, x, xnd, factor, active, smem, st);
+                             const int* active, size_t smem, bool overlap, cudaStream_t st) {
+  if (dbl) return run_t<double>(phases, a, lv, la, P, b, ynd, u, x, xnd, factor, active, smem, overlap, st);
+  return run_t<float>(phases, a, lv, la, P, b, ynd, u, x, xnd, factor, active, smem, overlap, st);
 }
 
 }  // namespace omm

@@ -65,8 +65,43 @@ struct SppPole {
   double sigma_min = 0, sigma_max = 0;   // singular values of G(a, a^c)
 };
 
+// The stencil data of one pole (eqs. GLu, QG, P): q, (qG)(0, a) and the mean potential l,
+// so that P(j, j + o_t) = q_t + qg_t (V_{j+o_t} - l).
+struct SppStencil {
+  std::vector<cd> q, qg;
+  double lmean = 0;
+  double sigma_min = 0, sigma_max = 0;   // singular values of G(a, a^c)
+};
+
+// Index maps of a multifrontal factorisation on the device, built once per structure.
+// Node s owns an nf x nf front (nf = ns + nb, row-major, unknowns then boundary) at
+// foff[s] in a pole's front workspace; its P entries are asm_pos / asm_src over
+// [asm_ptr[s], asm_ptr[s + 1]) (front position, natural row * na + stencil index t);
+// after the partial LU its trailing nb x nb block is the update matrix, which the parent
+// adds at the rows / columns emap[boff + a] of its own front.  ok is false when a front
+// position would receive two entries of P (grids too small for the stencil) or the tree
+// is not binary; the host factorisation then stays in use.
+struct SppFactorMaps {
+  std::vector<long long> foff;
+  long long front_size = 0;        // entries per pole
+  std::vector<int> child0, child1; // children in the host's order, -1 if none
+  std::vector<int> asm_ptr, asm_pos, asm_src;
+  std::vector<int> nbr;            // n * na: natural index of the stencil neighbour j + o_t
+  std::vector<int> emap;           // per boundary entry (layout of bnd)
+  std::vector<int> leaf_of;        // per node: its index among the banded leaves, or -1
+  bool ok = false;
+};
+
 // Builds the ND structure for an m^dim periodic grid and stencil radius r.
 SppStructure spp_build_structure(int dim, int m, int r);
+
+// The device factorisation's maps for a structure.
+SppFactorMaps spp_factor_maps(const SppStructure& st);
+
+// q, (qG)(0, a), l and the Green symbol of one pole (the part of spp_setup_pole before
+// the factorisation); ghat_out as for spp_setup_pole.
+void spp_pole_stencil(const SppStructure& st, double kin, const double* V, double shift, cd z, SppStencil& out,
+                      std::vector<cd>& ghat_out);
 
 // Per pole: q by the SVD of G(a, a^c), P assembly, multifrontal LU with static pivoting.
 // kin: (2 pi^2 / L^2); V: n reals; shift: sigma; z: pole.  ghat_out (n) receives

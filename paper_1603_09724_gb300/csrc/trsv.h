@@ -57,11 +57,13 @@ size_t trsv_smem_bytes(bool dbl, int max_ns, int max_nb);
 // b (ND order, S systems) -> x (natural order); ynd, u, xnd (ND order) work buffers, each
 // S x n except u (urows x S).  factor: P poles' blocks.
 // phases: bit 0 leaves forward, bit 1 levels forward, bit 2 levels backward, bit 3 leaves
-// backward (SPP_ALL = 15); the phases must run in that order.
+// backward (SPP_ALL = 15); the phases must run in that order.  overlap: every launch is a
+// programmatic dependent launch, whose prologue (factor values, index lists) runs while
+// the launch before it on the stream finishes.
 constexpr int SPP_LEAF_FWD = 1, SPP_LEVELS_FWD = 2, SPP_LEVELS_BWD = 4, SPP_LEAF_BWD = 8, SPP_ALL = 15;
 cudaError_t launch_spp_solve(int phases, bool dbl, const TrsvArgs& a, const TrsvLevels& lv, const LeafArgs& la, int P,
                              const void* b, void* ynd, void* u, void* x, void* xnd, const void* factor,
-                             const int* active, size_t smem, cudaStream_t st);
+                             const int* active, size_t smem, bool overlap, cudaStream_t st);
 
 // All supernode heights (leaves excluded when `leaves`) of one application, every pole of
 // the launch, in one cooperative launch with grid barriers between the phases; bar: 3

@@ -36,6 +36,7 @@ def test_host_only_entry_points_work_without_gpu():
     assert omm.lib.omm_strerror(omm.OMM_ESHIFT).decode().startswith("H - sigma")
     p = omm.default_params()
     assert p.gmres_m == 15 and p.gmres_cycles == 5 and abs(p.gmres_rtol - 1e-5) < 1e-20
+    assert p.launch_overlap == 1 and p.trsv_persistent == 0 and p.fixed_iters == 0
     z, w = omm.poles_fermi(-10.0, -2.0, -1.6, 8)
     assert z.shape == (8,)
     with pytest.raises(omm.OmmError):
@@ -69,6 +70,8 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     bad = omm.default_params(gmres_m=0)
     assert create(g, 2 * tmax, bad) == omm.OMM_EINVAL
     bad = omm.default_params(stencil_radius=2)
+    assert create(g, 2 * tmax, bad) == omm.OMM_EINVAL
+    bad = omm.default_params(launch_overlap=2)
     assert create(g, 2 * tmax, bad) == omm.OMM_EINVAL
     assert create(g, 2 * tmax, None, Np=0) == omm.OMM_EINVAL
     assert not h.value

@@ -167,3 +167,26 @@ def test_persistent_levels_match_per_height_launches(omm, prec):
         out.append(to_host(Y))
         s.close()
     assert rel_err(out[1], out[0]) < (1e-12 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("streams", [1, 0])
+def test_overlapped_launches_match_ordinary(omm, prec, streams):
+    """omm_params.launch_overlap = 1 (programmatic dependent launches in the triangular
+    solves) changes only when each launch is scheduled, not its arithmetic: the pole
+    expansion is bitwise that of ordinary launches, on one stream and on one per pole."""
+    m, N, P, L = 32, 16, 16, 10.0
+    V, sig, lam = small_case(m, L)
+    z, w = opoles.poles_conformal(lam[0], lam[N - 1], lam[N], P)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    R = to_dev(torch, gaussian_block(m * m, N, seed=61), dt)
+    out = []
+    for ov in (0, 1):
+        p = omm.default_params(precision=prec, gmres_m=4, gmres_cycles=2, gmres_fixed=1, launch_overlap=ov,
+                               trsv_streams=streams)
+        s = omm.Solver(2, m, L, V, N, shift=sig, params=p)
+        s.set_poles(z, w)
+        Y, st = s.pole_solve(R)
+        out.append(to_host(Y))
+        s.close()
+    assert np.array_equal(out[0], out[1])

@@ -35,11 +35,11 @@ def driver(tmp_path_factory):
     pytest.fail("host_spp_driver does not compile")
 
 
-def run_driver(exe, dim, m, L, V, shift, z, b, threads=1, raw=False):
+def run_driver(exe, dim, m, L, V, shift, z, b, threads=1, raw=False, extra=()):
     f = lambda v: repr(float(v))
     lines = [f"{dim} {m} {f(L)} {f(shift)} {f(z.real)} {f(z.imag)}", " ".join(f(v) for v in V),
              " ".join(f"{f(v.real)} {f(v.imag)}" for v in b)]
-    r = subprocess.run([exe, str(threads)], input="\n".join(lines) + "\n", capture_output=True, text=True,
+    r = subprocess.run([exe, str(threads), *extra], input="\n".join(lines) + "\n", capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     if raw:
@@ -86,3 +86,24 @@ def test_threaded_tree_factorisation_is_bitwise_identical(driver, dim, m, L):
     b = np.random.default_rng(7).standard_normal(n) + 1j * np.random.default_rng(8).standard_normal(n)
     outs = [run_driver(driver, dim, m, L, V, shift, z, b, threads=t, raw=True) for t in (1, 2, 4)]
     assert outs[0] == outs[1] == outs[2]
+
+
+@pytest.mark.parametrize("dim,m,L", [(2, 16, 10.0), (2, 32, 10.0), (3, 8, 20.0), (3, 12, 20.0)])
+def test_device_factor_maps_reproduce_the_host_factor(driver, dim, m, L):
+    """The index maps of the device factorisation (csrc/k_factor.cu) drive, replayed on the
+    host in FP64 with the device's own step order (fronts assembled from the maps, the
+    children's update matrices added through emap, unblocked partial LU, L_SS^-1 and U_SS^-1
+    by columns, the W products, the banded leaf data), a factor equal to the host
+    factorisation's to rounding: every W block and every leaf entry."""
+    shape = (m,) * dim
+    V = wells_2d(m, L, seed=6) if dim == 2 else lattice_wells_3d(m, L, cells=2)
+    shift = ham.default_shift(shape, L, V)
+    z = complex(-0.25 * shift, 0.9)
+    n = m ** dim
+    b = np.ones(n, dtype=complex)
+    out = run_driver(driver, dim, m, L, V, shift, z, b, raw=True, extra=("maps",))
+    line = [ln for ln in out.splitlines() if ln.startswith("mapsdiff")][0].split()
+    assert line[1] != "unsupported"
+    dfac, dleaf = float(line[1]), float(line[2])
+    assert dfac < 1e-11, dfac
+    assert dleaf < 1e-11, dleaf

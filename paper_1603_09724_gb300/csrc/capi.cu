@@ -204,7 +204,7 @@ struct omm_ctx {
   int *d_nbr = nullptr, *d_emap = nullptr, *d_leaf_of = nullptr, *d_hnodes = nullptr;
   double* d_Vdbl = nullptr;
   double2* d_qq = nullptr;                  // PMAX x 27 (q) then PMAX x 27 ((qG)(0, a))
-  std::vector<int> hn_start, hn_count, hn_tiles;   // per height: nodes and W-product tiles
+  std::vector<FactorHeight> fheights;       // per height: launch shapes (node ids in d_hnodes)
   bool last_factor_device = false;
   // algorithmic complex elements of the triangular-solve phases: per system and per pole
   double tb_leaf_fwd_sys = 0, tb_leaf_bwd_sys = 0, tb_leaf_pole = 0, tb_lvl_sys = 0, tb_lvl_pole = 0;
@@ -1241,22 +1241,42 @@ omm_status ensure_factor_maps(omm_ctx* h) {
   OMM_TRY(upload_vec(h, &h->d_leaf_of, mp.leaf_of));
   OMM_TRY(upload_vec(h, &h->d_Vdbl, h->Vh));
   OMM_TRY(h->dalloc_t(&h->d_qq, (size_t)2 * PMAX * 27 * sizeof(double2)));
-  std::vector<int> hn;
-  h->hn_start.clear();
-  h->hn_count.clear();
-  h->hn_tiles.clear();
+  std::vector<int> hn, start;
+  h->fheights.clear();
   for (const auto& lev : s.levels) {
-    h->hn_start.push_back((int)hn.size());
-    h->hn_count.push_back((int)lev.size());
-    int tiles = 0;
+    FactorHeight fh;
+    start.push_back((int)hn.size());
+    fh.count = (int)lev.size();
+    int max_ns = 0;
     for (int id : lev) {
-      const int tn = (s.nodes[id].ns + 31) / 32, tb = (s.nodes[id].nb + 31) / 32;
-      tiles = std::max(tiles, 2 * tn * tb);
+      const SppNode& nd = s.nodes[id];
+      max_ns = std::max(max_ns, nd.ns);
+      fh.max_nf = std::max(fh.max_nf, nd.ns + nd.nb);
+      if (mp.leaf_of[id] < 0) {
+        fh.dense_nodes = true;
+        fh.wprod_tiles = std::max(fh.wprod_tiles, 2 * ((nd.ns + 31) / 32) * ((nd.nb + 31) / 32));
+      } else {
+        fh.has_leaves = true;
+      }
     }
-    h->hn_tiles.push_back(tiles);
+    fh.max_ns = max_ns;
+    fh.npanels = (max_ns + 31) / 32;
+    if (fh.npanels > FactorHeight::kMaxPanels) return OMM_OK;   // stays with the host factorisation
+    for (int q = 0; q < fh.npanels; ++q) {
+      int tiles = 0;
+      for (int id : lev) {
+        const SppNode& nd = s.nodes[id];
+        if (q * 32 >= nd.ns) continue;
+        const int tm = (nd.ns + nd.nb - std::min(q * 32 + 32, nd.ns) + 31) / 32;
+        tiles = std::max(tiles, tm * tm);
+      }
+      fh.trail_tiles[q] = tiles;
+    }
+    h->fheights.push_back(fh);
     hn.insert(hn.end(), lev.begin(), lev.end());
   }
   OMM_TRY(upload_vec(h, &h->d_hnodes, hn));
+  for (size_t lh = 0; lh < h->fheights.size(); ++lh) h->fheights[lh].nodes = h->d_hnodes + start[lh];
   OMM_TRY(cuda_status(cudaStreamSynchronize(h->st), "maps sync"));
   h->front_size = mp.front_size;
   h->fmaps_ok = true;
@@ -1323,10 +1343,8 @@ omm_status device_factor(omm_ctx* h, int P, const std::vector<SppStencil>& sten)
     fa.q = h->d_qq;
     fa.qg = h->d_qq + (size_t)PMAX * 27;
     fa.pivot_floor = h->prm.pivot_floor;
-    for (size_t lh = 0; lh < s.levels.size() && rc == OMM_OK; ++lh)
-      rc = cuda_status(launch_factor_height(fa, h->d_hnodes + h->hn_start[lh], h->hn_count[lh], P, h->hn_tiles[lh],
-                                            fronts, fac64, leaf64, pst, h->st),
-                       "factor");
+    for (size_t lh = 0; lh < h->fheights.size() && rc == OMM_OK; ++lh)
+      rc = cuda_status(launch_factor_height(fa, h->fheights[lh], P, fronts, fac64, leaf64, pst, h->st), "factor");
     if (rc == OMM_OK && !h->dbl)
       rc = cuda_status(launch_factor_to_c64(fac64, (float2*)h->factor, nfac, h->st), "factor c64");
     if (rc == OMM_OK && !h->dbl && nleaf)
@@ -1431,6 +1449,8 @@ omm_status omm_set_poles(omm_t h, int P, const double* z, const double* w) {
       if (h->Pfac < P) {
         h->Pfac = 0;
         OMM_TRY(h->dalloc(&h->factor, (size_t)P * fs * h->csz));
+        // (the device factorisation leaves the unused W blocks of 2D leaves as they are)
+        OMM_TRY(cuda_status(cudaMemsetAsync(h->factor, 0, (size_t)P * fs * h->csz, h->st), "memset"));
         OMM_TRY(h->dalloc(&h->leafvals, (size_t)P * h->spp.leaf_size * h->csz));
         OMM_TRY(h->dalloc(&h->ubuf, (size_t)h->spp.urows * P * h->N * h->csz));
         OMM_TRY(h->dalloc(&h->ynd, (size_t)P * h->N * n * h->csz));

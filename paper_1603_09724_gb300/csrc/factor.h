@@ -39,15 +39,29 @@ struct FactorArgs {
   double pivot_floor;
 };
 
-// One tree height of the factorisation for P poles, in FP64: the `count` nodes listed at
-// `nodes` (device), all of whose children were factorised by earlier calls.  fronts:
-// P x front_size work space; factor / leafv: P x factor_size W blocks and P x leaf_size
-// banded leaf data, written for these nodes; pstats: P x nnodes x 3 doubles (smallest and
-// largest pivot magnitude, pivots raised).  max_tiles: largest number of 32 x 32 output
-// tiles of the W products over the nodes.  Errors: cudaErrorInvalidValue for P or count
-// outside [1, 65535].
-cudaError_t launch_factor_height(const FactorArgs& f, const int* nodes, int count, int P, int max_tiles,
-                                 double2* fronts, double2* factor, double2* leafv, double* pstats, cudaStream_t st);
+// The launch shape of one tree height (computed on the host from the node sizes).
+struct FactorHeight {
+  static constexpr int kMaxPanels = 64;   // panels of 32 pivots: ns up to 2048
+  const int* nodes = nullptr;   // device: node ids of the height
+  int count = 0;                // nodes
+  int max_ns = 0;               // largest ns of the height
+  int max_nf = 0;               // largest front (ns + nb) of the height
+  int npanels = 0;              // ceil(max_ns / 32)
+  int trail_tiles[kMaxPanels];  // per panel: largest count of 32 x 32 trailing-update tiles
+  bool has_leaves = false;      // some node of the height is a banded 2D leaf
+  bool dense_nodes = false;     // some node of the height needs its dense W blocks
+  int wprod_tiles = 0;          // largest count of 32 x 32 output tiles of the W products
+};
+
+// One tree height of the factorisation for P poles, in FP64: the nodes of hh, all of whose
+// children were factorised by earlier calls.  fronts: P x front_size work space;
+// factor / leafv: P x factor_size W blocks and P x leaf_size banded leaf data, written for
+// these nodes (a 2D leaf's W blocks are left as they are: the solves use its banded data);
+// pstats: P x nnodes x 3 doubles (smallest and largest pivot magnitude, pivots raised).
+// Errors: cudaErrorInvalidValue for P or count outside [1, 65535] or npanels above
+// kMaxPanels.
+cudaError_t launch_factor_height(const FactorArgs& f, const FactorHeight& hh, int P, double2* fronts,
+                                 double2* factor, double2* leafv, double* pstats, cudaStream_t st);
 
 // dst[i] = src[i] rounded to complex64 (a mixed handle's factor and leaf data).
 cudaError_t launch_factor_to_c64(const double2* src, float2* dst, size_t count, cudaStream_t st);

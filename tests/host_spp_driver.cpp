@@ -6,9 +6,11 @@
 //
 // argv[1] (optional): threads for the elimination tree (default 1)
 // argv[2] (optional): "maps" -- also replay the device factorisation's schedule
-//         (SppFactorMaps: fronts assembled from the maps, unblocked partial LU, L_SS^-1 and
-//         U_SS^-1 by columns, the W products) on the host and print "mapsdiff" with the
-//         largest differences from the host factor, relative to the largest entry
+//         (SppFactorMaps: fronts assembled from the maps, partial LU -- written unblocked:
+//         the device's panels and trailing updates give every element the same updates in
+//         the same order --, L_SS^-1 and U_SS^-1 by columns, the W products) on the host and
+//         print "mapsdiff" with the largest differences from the host factor, relative to
+//         the largest entry
 // stdin:  dim m L shift z_re z_im, then n values of V, then n pairs (re, im) of b
 // stdout: "dense" then n pairs of x (every node through W), and for 2D "banded" then n
 //         pairs of x (leaves through the banded data)

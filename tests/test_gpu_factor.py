@@ -28,7 +28,8 @@ def omm():
     return m
 
 
-CASES = [(2, 16, 10.0), (2, 32, 10.0), (2, 128, 10.0), (3, 8, 20.0), (3, 12, 20.0)]
+# 3D 16^3 has fronts of 736 rows: the panels of the LU stay in global memory there
+CASES = [(2, 16, 10.0), (2, 32, 10.0), (2, 128, 10.0), (3, 8, 20.0), (3, 12, 20.0), (3, 16, 40.0)]
 
 
 def setup(omm, dim, m, L, prec, device_factor):
@@ -46,6 +47,8 @@ def setup(omm, dim, m, L, prec, device_factor):
 def test_device_factor_matches_host_factor(omm, prec, dim, m, L):
     if prec == 0 and m == 128:
         pytest.skip("FP64 at 128^2 is covered by the 32^2 and 3D cases (the host FP64 factor takes seconds)")
+    if prec == 0 and dim == 3 and m == 16:
+        pytest.skip("FP64 handles take the sparsifying solve up to 12^3")
     n = m ** dim
     dt = torch.complex128 if prec == 0 else torch.complex64
     B = to_dev(torch, gaussian_block(n, 3, seed=11), dt)

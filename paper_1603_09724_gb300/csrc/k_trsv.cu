@@ -477,7 +477,9 @@ __device__ __forceinline__ void band_upper(cx_t<T>* y, int ns, int bw, const cx_
   }
 }
 
-// shared memory of one leaf CTA: y block, the leaf's values, its index lists
+// shared memory of one leaf CTA: y block, the leaf's values, the halo values of 32
+// columns (backward, stride LHS), its index lists
+constexpr int LHS = 33;
 __host__ __device__ inline size_t leaf_vals_count(int ns, int nb, int bw) {
   return (size_t)ns * bw + (size_t)ns * (bw + 1) + (size_t)nb * LNB + (size_t)ns * LNB;
 }
@@ -485,7 +487,7 @@ __host__ __device__ inline size_t leaf_idx_count(int ns, int nb) { return (size_
 
 template <typename T>
 size_t leaf_smem_bytes(int max_ns, int max_nb, int bw) {
-  return ((size_t)max_ns * LDY + leaf_vals_count(max_ns, max_nb, bw)) * sizeof(cx_t<T>) +
+  return ((size_t)max_ns * LDY + leaf_vals_count(max_ns, max_nb, bw) + (size_t)max_nb * LHS) * sizeof(cx_t<T>) +
          leaf_idx_count(max_ns, max_nb) * sizeof(int);
 }
 
@@ -506,7 +508,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
   const int bw = la.bw;
   C* ys = reinterpret_cast<C*>(smem_raw);                                    // [ns][LDY]
   C* vs = ys + (size_t)la.max_ns * LDY;                                       // Lb | Ub | Fbs | Fsb
-  int* is = reinterpret_cast<int*>(vs + leaf_vals_count(la.max_ns, la.max_nb, bw));
+  C* hs = vs + leaf_vals_count(la.max_ns, la.max_nb, bw);                   // [max_nb][LHS]
+  int* is = reinterpret_cast<int*>(hs + (size_t)la.max_nb * LHS);
   int* iperm = is;                  // natural index of leaf unknown i
   int* ibnd = iperm + ns;           // ND index of halo unknown j
   int* ibs = ibnd + nb;            // F_BS columns (leaf unknowns) per halo row, -1 padded
@@ -591,35 +594,27 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
       u[(size_t)(uoff + j) * a.S + s0 + tid] = acc;
     }
   } else {
-    // F_SB x_B: each lane's row (its couplings and halo positions read once) for 4 columns
-    constexpr int HQ = 4;
-    for (int i0 = 0; i0 < ns; i0 += 64)
-      for (int cb = wq; cb < LT; cb += NWQ * HQ)
+    // F_SB x_B, 32 columns at a time: the chunk's halo values are staged in shared memory
+    // (lanes along the halo unknowns, which lie in runs of the ND order), then each warp
+    // takes rows and its lanes the chunk's columns
+    for (int cb = 0; cb < LT; cb += 32) {
+      for (int c = wq; c < 32; c += NWQ) {
+        const bool on = live[cb + c];
+        const C* xs = xnd + (s0 + cb + c) * a.n;
+        for (int j = lane; j < nb; j += 32) hs[j * LHS + c] = on ? xs[ibnd[j]] : mk<C>(0, 0);
+      }
+      __syncthreads();
+      for (int i = wq; i < ns; i += NWQ) {
+        C acc = mk<C>(0, 0);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = i0 + lane + 32 * h;
-          if (i >= ns) continue;
-          C acc[HQ];
-          bool on[HQ];
-#pragma unroll
-          for (int q = 0; q < HQ; ++q) {
-            acc[q] = mk<C>(0, 0);
-            on[q] = live[cb + q * NWQ];
-          }
-#pragma unroll
-          for (int t = 0; t < LNB; ++t) {   // -1 entries trail: same order as a breaking loop
-            const int j = isb[i * LNB + t];
-            if (j < 0) continue;
-            const C f = Fsb[i * LNB + t];
-            const int bj = ibnd[j];
-#pragma unroll
-            for (int q = 0; q < HQ; ++q)
-              if (on[q]) acc[q] = cfma(f, xnd[(s0 + cb + q * NWQ) * a.n + bj], acc[q]);
-          }
-#pragma unroll
-          for (int q = 0; q < HQ; ++q)
-            if (on[q]) ys[i * LDY + cb + q * NWQ] = acc[q];
+        for (int t = 0; t < LNB; ++t) {   // -1 entries trail: same order as a breaking loop
+          const int j = isb[i * LNB + t];
+          if (j >= 0) acc = cfma(Fsb[i * LNB + t], hs[j * LHS + lane], acc);
         }
+        if (live[cb + lane]) ys[i * LDY + cb + lane] = acc;
+      }
+      __syncthreads();
+    }
     __syncthreads();
     if (mine) band_lower<T>(y, ns, bw, Lb);
     __syncthreads();

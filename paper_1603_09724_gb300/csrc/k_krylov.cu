@@ -207,6 +207,100 @@ __global__ void __launch_bounds__(KT) krylov_orth_kernel(KrylovDims d, cx_t<T>* 
   }
 }
 
+// The same CGS2 for complex64 bases with an even grid size: every thread moves two
+// consecutive complex values per 16-byte load (float4), so twice the bytes are in flight
+// per instruction on the three streaming sweeps.
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+
+template <int KK>
+__global__ void __launch_bounds__(KT) krylov_orth_c64x2_kernel(KrylovDims d, float2* __restrict__ V,
+                                                               const float2* __restrict__ w, double2* __restrict__ H,
+                                                               const int* __restrict__ active) {
+  using C = float2;
+  constexpr int k = KK - 1;
+  __shared__ double sh[(2 * KK + 1) * (KT / 32)];
+  const int s = blockIdx.x;
+  if (!active[s]) return;
+  const size_t n2 = d.n / 2;
+  const size_t vs2 = (size_t)d.S * n2;   // stride between basis vectors, in pairs
+  const float4* ws = reinterpret_cast<const float4*>(w) + (size_t)s * n2;
+  const float4* Vs = reinterpret_cast<const float4*>(V) + (size_t)s * n2;
+  double h[2 * KK + 1];
+  C ht[KK];
+  C h1c[KK];
+  // sweep 1: h1 = V^H w
+#pragma unroll
+  for (int q = 0; q < KK; ++q) ht[q] = mk<C>(0, 0);
+  for (size_t i = threadIdx.x; i < n2; i += KT) {
+    const float4 wi = ws[i];
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+      const float4 v = Vs[j * vs2 + i];
+      ht[j] = cfmac(hi2(v), hi2(wi), cfmac(lo2(v), lo2(wi), ht[j]));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KK; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
+  h[2 * KK] = 0.0;
+  block_reduce<2 * KK + 1>(h, sh);
+  double h1[2 * KK];
+#pragma unroll
+  for (int q = 0; q < 2 * KK; ++q) h1[q] = h[q];
+#pragma unroll
+  for (int j = 0; j < KK; ++j) h1c[j] = mk<C>((float)h1[2 * j], (float)h1[2 * j + 1]);
+  // sweep 2: w' = w - V h1 on the fly, h2 = V^H w', |w'|^2
+#pragma unroll
+  for (int q = 0; q < KK; ++q) ht[q] = mk<C>(0, 0);
+  float nw = 0;
+  for (size_t i = threadIdx.x; i < n2; i += KT) {
+    const float4 wi = ws[i];
+    C wa = lo2(wi), wb = hi2(wi);
+    float4 vv[KK];
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+      vv[j] = Vs[j * vs2 + i];
+      wa = csub(wa, cmul(h1c[j], lo2(vv[j])));
+      wb = csub(wb, cmul(h1c[j], hi2(vv[j])));
+    }
+#pragma unroll
+    for (int j = 0; j < KK; ++j) ht[j] = cfmac(hi2(vv[j]), wb, cfmac(lo2(vv[j]), wa, ht[j]));
+    nw += wa.x * wa.x + wa.y * wa.y + wb.x * wb.x + wb.y * wb.y;
+  }
+#pragma unroll
+  for (int q = 0; q < KK; ++q) { h[2 * q] = (double)ht[q].x; h[2 * q + 1] = (double)ht[q].y; }
+  h[2 * KK] = (double)nw;
+  block_reduce<2 * KK + 1>(h, sh);
+  double h2sq = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2 * KK; ++q) {
+    h2sq += h[q] * h[q];
+    h1[q] += h[q];
+  }
+  const double hn = sqrt(fmax(h[2 * KK] - h2sq, 0.0));
+  const float inv = hn > 0.0 ? (float)(1.0 / hn) : 0.f;
+#pragma unroll
+  for (int j = 0; j < KK; ++j) h1c[j] = mk<C>((float)h1[2 * j], (float)h1[2 * j + 1]);
+  // sweep 3: V_{k+1} = (w - V (h1 + h2)) / |w''|
+  float4* vk1 = reinterpret_cast<float4*>(V) + (size_t)(k + 1) * vs2 + (size_t)s * n2;
+  for (size_t i = threadIdx.x; i < n2; i += KT) {
+    const float4 wi = ws[i];
+    C wa = lo2(wi), wb = hi2(wi);
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+      const float4 v = Vs[j * vs2 + i];
+      wa = csub(wa, cmul(h1c[j], lo2(v)));
+      wb = csub(wb, cmul(h1c[j], hi2(v)));
+    }
+    vk1[i] = make_float4(wa.x * inv, wa.y * inv, wb.x * inv, wb.y * inv);
+  }
+  if (threadIdx.x == 0) {
+    double2* Hs = H + (size_t)s * (KMAX + 1) * KMAX;
+    for (int j = 0; j <= k; ++j) Hs[j * KMAX + k] = make_double2(h1[2 * j], h1[2 * j + 1]);
+    Hs[(k + 1) * KMAX + k] = make_double2(hn, 0.0);
+  }
+}
+
 template <typename T>
 static cudaError_t orth_dispatch(KrylovDims d, int k, void* V, void* w, double2* H, const int* active,
                                  cudaStream_t st) {
@@ -215,6 +309,21 @@ static cudaError_t orth_dispatch(KrylovDims d, int k, void* V, void* w, double2*
   case KK_:                                                                                              \
     krylov_orth_kernel<T, KK_><<<d.S, KT, 0, st>>>(d, (C*)V, (const C*)w, H, active);                    \
     break;
+  // complex64 with an even grid: paired loads, up to 10 basis vectors (beyond, the paired
+  // kernel needs more than 128 registers and would halve the CTAs per SM)
+  if (sizeof(C) == sizeof(float2) && d.n % 2 == 0 && k + 1 <= 10) {
+#define ORTH2_CASE(KK_)                                                                                  \
+  case KK_:                                                                                              \
+    krylov_orth_c64x2_kernel<KK_><<<d.S, KT, 0, st>>>(d, (float2*)V, (const float2*)w, H, active);       \
+    break;
+    switch (k + 1) {
+      ORTH2_CASE(1) ORTH2_CASE(2) ORTH2_CASE(3) ORTH2_CASE(4) ORTH2_CASE(5) ORTH2_CASE(6) ORTH2_CASE(7)
+      ORTH2_CASE(8) ORTH2_CASE(9) ORTH2_CASE(10)
+      default: return cudaErrorInvalidValue;
+    }
+#undef ORTH2_CASE
+    return cudaGetLastError();
+  }
   switch (k + 1) {
     ORTH_CASE(1) ORTH_CASE(2) ORTH_CASE(3) ORTH_CASE(4) ORTH_CASE(5) ORTH_CASE(6) ORTH_CASE(7) ORTH_CASE(8)
     ORTH_CASE(9) ORTH_CASE(10) ORTH_CASE(11) ORTH_CASE(12) ORTH_CASE(13) ORTH_CASE(14) ORTH_CASE(15)

@@ -441,7 +441,9 @@ constexpr int LGB = 8;        // gathered loads in flight per thread
 // Band substitutions, one right-hand side per thread on its column of y (stride LDY).
 // The band loops are unrolled to kMaxBw with the rows near the ends predicated, and each
 // term is two fused multiply-adds per component (acc - l y), so a row costs about 4 bw FMA
-// instructions and no loop control.
+// instructions and no loop control.  The last kMaxBw solved values stay in registers: the
+// rows are unrolled in groups of kMaxBw, so row i of a group keeps its value in slot
+// (i - first row) of the window and reads its neighbours' values from fixed slots.
 constexpr int kMaxBw = 9;   // leaves of at most 8 x 8 points (x-fastest order: band <= 9)
 
 template <typename C>
@@ -453,27 +455,46 @@ __device__ __forceinline__ C cfms(C l, C y, C acc) {   // acc - l * y
 
 template <typename T>
 __device__ __forceinline__ void band_lower(cx_t<T>* y, int ns, int bw, const cx_t<T>* Lb) {
-  for (int i = 0; i < ns; ++i) {
-    cx_t<T> acc = y[i * LDY];
-    const cx_t<T>* lr = Lb + i * bw;
-    const int tn = min(bw, i);
+  using C = cx_t<T>;
+  C win[kMaxBw];   // win[(i - i0) % kMaxBw] = y_i
+  for (int i0 = 0; i0 < ns; i0 += kMaxBw) {
 #pragma unroll
-    for (int t = 0; t < kMaxBw; ++t)
-      if (t < tn) acc = cfms(lr[t], y[(i - 1 - t) * LDY], acc);
-    y[i * LDY] = acc;
+    for (int r = 0; r < kMaxBw; ++r) {
+      const int i = i0 + r;
+      if (i < ns) {
+        C acc = y[i * LDY];
+        const C* lr = Lb + i * bw;
+        const int tn = min(bw, i);
+#pragma unroll
+        for (int t = 0; t < kMaxBw; ++t)   // y_{i-1-t} sits in slot (r - 1 - t) mod kMaxBw
+          if (t < tn) acc = cfms(lr[t], win[(r - 1 - t + 2 * kMaxBw) % kMaxBw], acc);
+        win[r] = acc;
+        y[i * LDY] = acc;
+      }
+    }
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void band_upper(cx_t<T>* y, int ns, int bw, const cx_t<T>* Ub) {
-  for (int i = ns - 1; i >= 0; --i) {
-    cx_t<T> acc = y[i * LDY];
-    const cx_t<T>* ur = Ub + i * (bw + 1);
-    const int tn = min(bw, ns - 1 - i);
+  using C = cx_t<T>;
+  C win[kMaxBw];   // win[(i1 - i) % kMaxBw] = x_i, rows taken downwards from i1
+  for (int i1 = ns - 1; i1 >= 0; i1 -= kMaxBw) {
 #pragma unroll
-    for (int t = 1; t <= kMaxBw; ++t)
-      if (t <= tn) acc = cfms(ur[t], y[(i + t) * LDY], acc);
-    y[i * LDY] = cmul(ur[0], acc);
+    for (int r = 0; r < kMaxBw; ++r) {
+      const int i = i1 - r;
+      if (i >= 0) {
+        C acc = y[i * LDY];
+        const C* ur = Ub + i * (bw + 1);
+        const int tn = min(bw, ns - 1 - i);
+#pragma unroll
+        for (int t = 1; t <= kMaxBw; ++t)   // x_{i+t} sits in slot (r - t) mod kMaxBw
+          if (t <= tn) acc = cfms(ur[t], win[(r - t + 2 * kMaxBw) % kMaxBw], acc);
+        acc = cmul(ur[0], acc);
+        win[r] = acc;
+        y[i * LDY] = acc;
+      }
+    }
   }
 }
 

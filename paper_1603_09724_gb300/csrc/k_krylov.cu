@@ -311,7 +311,8 @@ static cudaError_t orth_dispatch(KrylovDims d, int k, void* V, void* w, double2*
     break;
   // complex64 with an even grid: paired loads, up to 10 basis vectors (beyond, the paired
   // kernel needs more than 128 registers and would halve the CTAs per SM)
-  if (sizeof(C) == sizeof(float2) && d.n % 2 == 0 && k + 1 <= 10) {
+  if (sizeof(C) == sizeof(float2) && d.n % 2 == 0 && k + 1 <= 10 && (uintptr_t)V % 16 == 0 &&
+      (uintptr_t)w % 16 == 0) {
 #define ORTH2_CASE(KK_)                                                                                  \
   case KK_:                                                                                              \
     krylov_orth_c64x2_kernel<KK_><<<d.S, KT, 0, st>>>(d, (float2*)V, (const float2*)w, H, active);       \
@@ -455,11 +456,43 @@ __global__ void __launch_bounds__(KT) krylov_xupdate_kernel(KrylovDims d, const 
   }
 }
 
+// complex64 with an even grid: two entries per 16-byte load
+__global__ void __launch_bounds__(KT) krylov_xupdate_c64x2_kernel(KrylovDims d, const int* __restrict__ steps,
+                                                                  const double2* __restrict__ y,
+                                                                  const float4* __restrict__ Z, float4* __restrict__ x) {
+  const int s = blockIdx.x;
+  const int k = steps[s];
+  if (k == 0) return;
+  const size_t n2 = d.n / 2, vs2 = (size_t)d.S * n2;
+  float2 yy[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    const double2 v = j < k ? y[(size_t)s * KMAX + j] : make_double2(0.0, 0.0);
+    yy[j] = make_float2((float)v.x, (float)v.y);
+  }
+  const float4* Zs = Z + (size_t)s * n2;
+  float4* xs = x + (size_t)s * n2;
+  for (size_t i = threadIdx.x; i < n2; i += KT) {
+    const float4 x0 = xs[i];
+    float2 a = make_float2(x0.x, x0.y), b = make_float2(x0.z, x0.w);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) {
+        const float4 z = Zs[j * vs2 + i];
+        a = cfma(yy[j], make_float2(z.x, z.y), a);
+        b = cfma(yy[j], make_float2(z.z, z.w), b);
+      }
+    xs[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 cudaError_t launch_krylov_update(bool dbl, KrylovDims d, const double2* H, const double2* g, const int* steps,
                                  double2* y, const void* Z, void* x, int* itot, cudaStream_t st) {
   krylov_backsolve_kernel<<<(d.S + 127) / 128, 128, 0, st>>>(d, H, g, steps, y, itot);
   if (dbl)
     krylov_xupdate_kernel<double><<<d.S, KT, 0, st>>>(d, steps, y, (const double2*)Z, (double2*)x);
+  else if (d.n % 2 == 0 && (uintptr_t)Z % 16 == 0 && (uintptr_t)x % 16 == 0)
+    krylov_xupdate_c64x2_kernel<<<d.S, KT, 0, st>>>(d, steps, y, (const float4*)Z, (float4*)x);
   else
     krylov_xupdate_kernel<float><<<d.S, KT, 0, st>>>(d, steps, y, (const float2*)Z, (float2*)x);
   return cudaGetLastError();
@@ -470,17 +503,34 @@ template <typename T>
 __global__ void pole_combine_kernel(KrylovDims d, int P, const double2* __restrict__ w, double sign, int real_part,
                                     const cx_t<T>* __restrict__ x, cx_t<T>* __restrict__ out) {
   using C = cx_t<T>;
-  const size_t total = (size_t)d.N * d.n;
+  const size_t total = (size_t)d.N * d.n;   // entry e of pole p's block sits at p * total + e
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t c = e / d.n, i = e % d.n;
     C acc = mk<C>(0, 0);
     for (int p = 0; p < P; ++p) {
       const double2 wp = w[p];
       const C wc = mk<C>((T)(sign * wp.x), (T)(sign * wp.y));
-      acc = cfma(wc, x[((size_t)p * d.N + c) * d.n + i], acc);
+      acc = cfma(wc, x[(size_t)p * total + e], acc);
     }
     if (real_part) acc.y = 0;
     out[e] = acc;
+  }
+}
+
+// complex64 with an even number of entries: two entries per 16-byte load
+__global__ void pole_combine_c64x2_kernel(KrylovDims d, int P, const double2* __restrict__ w, double sign,
+                                          int real_part, const float4* __restrict__ x, float4* __restrict__ out) {
+  const size_t total2 = (size_t)d.N * d.n / 2;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total2; e += (size_t)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f), b = a;
+    for (int p = 0; p < P; ++p) {
+      const double2 wp = w[p];
+      const float2 wc = make_float2((float)(sign * wp.x), (float)(sign * wp.y));
+      const float4 v = x[(size_t)p * total2 + e];
+      a = cfma(wc, make_float2(v.x, v.y), a);
+      b = cfma(wc, make_float2(v.z, v.w), b);
+    }
+    if (real_part) a.y = b.y = 0.f;
+    out[e] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
@@ -490,6 +540,8 @@ cudaError_t launch_pole_combine(bool dbl, KrylovDims d, int P, const double2* w,
   const int blocks = (int)((total + 255) / 256 < 4864 ? (total + 255) / 256 : 4864);
   if (dbl)
     pole_combine_kernel<double><<<blocks, 256, 0, st>>>(d, P, w, sign, real_part, (const double2*)x, (double2*)out);
+  else if (total % 2 == 0 && (uintptr_t)x % 16 == 0 && (uintptr_t)out % 16 == 0)
+    pole_combine_c64x2_kernel<<<blocks, 256, 0, st>>>(d, P, w, sign, real_part, (const float4*)x, (float4*)out);
   else
     pole_combine_kernel<float><<<blocks, 256, 0, st>>>(d, P, w, sign, real_part, (const float2*)x, (float2*)out);
   return cudaGetLastError();

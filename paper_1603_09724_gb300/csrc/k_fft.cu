@@ -95,6 +95,42 @@ greenq_kernel(const cx_t<T>* __restrict__ B, cx_t<T>* __restrict__ Out, const cx
   __syncthreads();
   fft::transform<+1, LY, G::MZ, NT>(s, t, t, t);
   C* o = Out + (size_t)col * G::N;
+  if constexpr (D == 2 && NT % M == 0 && M % (NT / M) == 0) {
+    if (nq == 9) {
+      // the 3 x 3 box in 2D: each thread walks a strip of RPS consecutive rows of one grid
+      // column with the three rows around the current one in registers, so each output
+      // reads three new values (same terms, same order as the loop below)
+      constexpr int RPS = M / (NT / M);
+      const int ix = threadIdx.x % M, y0 = (threadIdx.x / M) * RPS;
+      const int xm = (ix + M - 1) % M, xp = (ix + 1) % M;
+      C w[3][3];
+      auto row = [&](int yy, C* v) {
+        v[0] = s[LY::at(xm, yy, 0)];
+        v[1] = s[LY::at(ix, yy, 0)];
+        v[2] = s[LY::at(xp, yy, 0)];
+      };
+      row((y0 + M - 1) % M, w[0]);
+      row(y0, w[1]);
+#pragma unroll 4
+      for (int rr = 0; rr < RPS; ++rr) {
+        const int y = y0 + rr;
+        row((y + 1) % M, w[2]);
+        C acc = mk<C>(0, 0);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) acc = cfma(qs[dy * 3 + dx], w[dy][dx], acc);
+        const int i = y * M + ix;
+        o[iperm ? iperm[i] : i] = acc;
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          w[0][dx] = w[1][dx];
+          w[1][dx] = w[2][dx];
+        }
+      }
+      return;
+    }
+  }
   const int r = (nq == 1) ? 0 : 1;   // delta stencil (kinetic inverse only) or the 3^d box
   for (int i = threadIdx.x; i < G::N; i += NT) {
     const int ix = i % M, iy = (i / M) % M, iz = i / (M * M);

@@ -549,14 +549,25 @@ def roofline_record(prof, dom, wl, peaks, sm_mhz, gram_tensor, apps):
         "orth": "(2(k+1) + 3) x n x 8 B per active system at Arnoldi step k",
     }.get(dom, "the library's algorithmic byte count")
     tr = TRAFFIC_PER_CALL.get((getattr(wl, "name", None), N, dom))
-    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": tr,
-            "algorithmic_bytes_per_call": per_call,
-            "impl_bytes_per_call": d.get("impl_bytes", d["bytes"]) / max(d["calls"], 1),
-            "note": (f"achieved = algorithmic bytes / CUDA-event time summed over the class's launches in one "
-                     f"untimed profile solve ({formula}); a call is one application of the class to all "
-                     f"systems (one GMRES step's triangular solves, H-apply, ...); peak = measured copy bandwidth "
-                     f"(of measured); traffic = DRAM bytes per call from ncu, or null")}
+    rec = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+           "traffic": tr,
+           "algorithmic_bytes_per_call": per_call,
+           "impl_bytes_per_call": d.get("impl_bytes", d["bytes"]) / max(d["calls"], 1),
+           "note": (f"achieved = algorithmic bytes / CUDA-event time summed over the class's launches in one "
+                    f"untimed profile solve ({formula}); a call is one application of the class to all "
+                    f"systems (one GMRES step's triangular solves, H-apply, ...); peak = measured copy bandwidth "
+                    f"(of measured); traffic = DRAM bytes per call from ncu, or null")}
+    if d.get("flops", 0.0) > 0.0:
+        # the same class against FP32 FMA: its dense supernode products carry about 128 flops
+        # per byte of W, so the arithmetic bound lies far below the byte bound
+        mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
+        fpk = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        fach = d["flops"] / ms / 1e9
+        rec["alu"] = {"achieved": fach, "peak": fpk, "unit": "TFLOP/s", "frac": fach / fpk,
+                      "flops_per_call": d["flops"] / max(d["calls"], 1),
+                      "note": f"8 real flops per W_f / W_b entry and active system of its pole; peak = FP32 FMA "
+                              f"on the CUDA cores at {mhz:.0f} MHz ({SMS} SMs x {FP32_LANES_PER_SM} lanes x 2)"}
+    return rec
 
 
 def precond_text(a, spectra):

@@ -399,6 +399,12 @@ omm_status omm_device_bytes(omm_t h, size_t* bytes);
 omm_status omm_profile_enable(omm_t h, int on);
 omm_status omm_profile_read(omm_t h, int cls, long long* calls, long long* kernels, double* ms, double* bytes);
 omm_status omm_profile_read_impl(omm_t h, int cls, double* impl_bytes);
+/* Algorithmic real flops counted for a class since the last omm_profile_enable: the
+ * supernode products of the triangular solves (class 2: 8 flops per W_f or W_b entry of a
+ * pole and active system of that pole, Sec. 3.2's dense supernode blocks); 0 for the
+ * classes whose bound is memory traffic.  Errors: OMM_EINVAL (NULL handle or output, class
+ * out of range). */
+omm_status omm_profile_read_flops(omm_t h, int cls, double* flops);
 const char* omm_profile_class_name(int cls);
 
 #ifdef __cplusplus

@@ -86,6 +86,7 @@ _SIGS = {
     "omm_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _dp, _dp]),
     "omm_profile_class_name": (C.c_char_p, [C.c_int]),
     "omm_profile_read_impl": (C.c_int, [_vp, C.c_int, _dp]),
+    "omm_profile_read_flops": (C.c_int, [_vp, C.c_int, _dp]),
     "omm_gram_noalloc": (C.c_int, [C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_size_t, _vp, _vp]),
 }
 PROFILE_CLASSES = ("happly", "greenq", "trsv_levels", "orth", "gram", "block_update", "vector", "small", "trsv_leaf")
@@ -342,9 +343,11 @@ class Solver:
             calls, kern, ms, by = C.c_longlong(), C.c_longlong(), C.c_double(), C.c_double()
             check(lib.omm_profile_read(self.h, c, C.byref(calls), C.byref(kern), C.byref(ms), C.byref(by)),
                   "omm_profile_read")
-            ib = C.c_double()
+            ib, fl = C.c_double(), C.c_double()
             check(lib.omm_profile_read_impl(self.h, c, C.byref(ib)), "omm_profile_read_impl")
-            out[name] = dict(calls=calls.value, kernels=kern.value, ms=ms.value, bytes=by.value, impl_bytes=ib.value)
+            check(lib.omm_profile_read_flops(self.h, c, C.byref(fl)), "omm_profile_read_flops")
+            out[name] = dict(calls=calls.value, kernels=kern.value, ms=ms.value, bytes=by.value, impl_bytes=ib.value,
+                             flops=fl.value)
         return out
 
     def device_bytes(self):

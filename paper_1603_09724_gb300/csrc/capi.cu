@@ -54,6 +54,7 @@ struct Prof {
   long long kernels[PC_NCLS] = {};
   double bytes[PC_NCLS] = {};        // algorithmic bytes (what the step must move)
   double impl_bytes[PC_NCLS] = {};   // this implementation's own byte model (intermediates included)
+  double flops[PC_NCLS] = {};        // algorithmic real flops (classes whose bound is arithmetic)
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, size_t>> pending;   // class, first event index
@@ -615,6 +616,9 @@ omm_status inner_apply(omm_ctx* h, int P, int Ncols, const void* Vk, void* Z, co
   if (has_leaves)
     PROF2(PC_TRSV_LEAF, (2.0 * h->n_leaf * Se + 0.5 * h->tb_leaf_pole * P) * cs,
           (h->tb_leaf_fwd_sys * Se + h->tb_leaf_pole * P) * cs, ns, spp(SPP_LEAF_FWD));
+  // the supernode products: every W_f and W_b entry of a pole times each of its active
+  // systems, 8 real flops per complex multiply-add
+  h->prof.flops[PC_TRSV] += 8.0 * h->tb_lvl_pole * Se;
   PROF2(PC_TRSV, (4.0 * h->n_sep * Se + h->tb_lvl_pole * P) * cs, (h->tb_lvl_sys * Se + h->tb_lvl_pole * P) * cs,
         ns * nk, spp(SPP_LEVELS_FWD | SPP_LEVELS_BWD));
   if (has_leaves)
@@ -1988,9 +1992,16 @@ omm_status omm_profile_enable(omm_t h, int on) {
       h->prof.kernels[c] = 0;
       h->prof.bytes[c] = 0.0;
       h->prof.impl_bytes[c] = 0.0;
+      h->prof.flops[c] = 0.0;
     }
   }
   h->prof.on = on == 1;
+  return OMM_OK;
+}
+
+omm_status omm_profile_read_flops(omm_t h, int cls, double* flops) {
+  if (!h || !flops || cls < 0 || cls >= PC_NCLS) return OMM_EINVAL;
+  *flops = h->prof.flops[cls];
   return OMM_OK;
 }
 

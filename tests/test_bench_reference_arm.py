@@ -43,6 +43,14 @@ def test_roofline_record_bounds_and_arithmetic():
     # per call of the class: the algorithmic and the implementation's own bytes
     assert abs(r["algorithmic_bytes_per_call"] - 1.0e8) < 1e-3
     assert abs(r["impl_bytes_per_call"] - 3.0e8) < 1e-3
+    assert "alu" not in r                      # no flops counted: no arithmetic sub-record
+    # with the library's flop count of the supernode products: the same class against FP32 FMA
+    prof["trsv_levels"]["flops"] = 4.0e10
+    r = bench.roofline_record(prof, "trsv_levels", wl, peaks, 2070.0, 0, 5)
+    assert r["bound"] == "hbm" and r["alu"]["unit"] == "TFLOP/s"
+    assert abs(r["alu"]["achieved"] - 4.0e10 / 2.0e-3 / 1e12) < 1e-9
+    assert abs(r["alu"]["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    assert abs(r["alu"]["flops_per_call"] - 4.0e9) < 1e-3
     r = bench.roofline_record(prof, "gram", wl, peaks, 2000.0, 0, 5)
     flops = 4 * 48.0 * 16384 * 128 ** 2
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"

@@ -91,6 +91,8 @@ struct omm_ctx {
   void* Gp = nullptr;
   double2* gram = nullptr;  // 2N x 4N
   void* gram_work = nullptr;
+  void* sc_block = nullptr;     // OmmScalars, then the line search's scratch
+  double* ls_work = nullptr;    // N x 12 doubles: partial traces of the line search
   void* M1 = nullptr;
   void* M2 = nullptr;
   OmmScalars* sc = nullptr;
@@ -797,7 +799,7 @@ omm_status start_cg(omm_ctx* h) {
   PROF(PC_GRAM, 5.0 * h->N * h->n * h->csz, 2,
        gram_any(h, h->X(), h->N, h->blk, 4 * h->N, h->gram, 4 * h->N, h->gram_work));
   PROF(PC_SMALL, 0, 1,
-       cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 0, h->prm.tol, h->sc, h->M1, h->M2, h->st),
+       cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 0, h->prm.tol, h->sc, h->M1, h->M2, h->ls_work, h->st),
                    "ls0"));
   return OMM_OK;
 }
@@ -830,7 +832,7 @@ omm_status cg_steps(omm_ctx* h, int k, omm_stats* st, int* done_iters, bool* con
     OMM_TRY(happly(h, h->D(), h->HD(), h->N, h->zero_shift, h->N, nullptr));
     PROF(PC_GRAM, 6.0 * cnt * h->csz, 2, gram_any(h, h->blk, 2 * h->N, h->blk, 4 * h->N, h->gram, 4 * h->N, h->gram_work));
     PROF(PC_SMALL, 0, 1,
-         cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->st),
+         cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->ls_work, h->st),
                      "ls"));
     // X += t D ; HX += t HD
     PROF(PC_VEC, 3.0 * cnt * h->csz, 1,
@@ -1161,7 +1163,11 @@ omm_status omm_create(const omm_grid* g, const double* V, int N, double shift, c
     return fail(s);
   if ((s = h->dalloc(&h->M1, (size_t)N * N * h->csz)) != OMM_OK) return fail(s);
   if ((s = h->dalloc(&h->M2, (size_t)N * N * h->csz)) != OMM_OK) return fail(s);
-  if ((s = h->dalloc_t(&h->sc, sizeof(OmmScalars))) != OMM_OK) return fail(s);
+  // the CG scalars, then the line search's per-row partial traces (N x 12 doubles)
+  const size_t sc_bytes = (sizeof(OmmScalars) + 255) / 256 * 256;
+  if ((s = h->dalloc(&h->sc_block, sc_bytes + (size_t)N * 12 * sizeof(double))) != OMM_OK) return fail(s);
+  h->sc = (OmmScalars*)h->sc_block;
+  h->ls_work = (double*)((char*)h->sc_block + sc_bytes);
   if ((s = h->dalloc(&h->red_work, redot_work_bytes())) != OMM_OK) return fail(s);
   if ((s = h->dalloc_t(&h->shifts, PMAX * sizeof(double2))) != OMM_OK) return fail(s);
   if ((s = h->dalloc_t(&h->zero_shift, sizeof(double2))) != OMM_OK) return fail(s);
@@ -1691,7 +1697,7 @@ omm_status omm_quartic(omm_t h, const void* X, const void* D, double* c, double*
   OMM_TRY(happly(h, h->X(), h->HX(), h->N, h->zero_shift, h->N, nullptr));
   OMM_TRY(happly(h, h->D(), h->HD(), h->N, h->zero_shift, h->N, nullptr));
   OMM_TRY(gram_any(h, h->blk, 2 * h->N, h->blk, 4 * h->N, h->gram, 4 * h->N, h->gram_work));
-  OMM_TRY(cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->st),
+  OMM_TRY(cuda_status(launch_line_search(h->dbl, h->gram, h->N, h->shift, 1, h->prm.tol, h->sc, h->M1, h->M2, h->ls_work, h->st),
                       "ls"));
   OMM_TRY(read_scalars(h));
   if (c)

@@ -7,6 +7,8 @@
 // t is one of the real roots of E'(t) (a cubic); c4 = -1/2 tr(C C_H) > 0 for H < 0.
 // H = H0 - sigma: the Grams come from the unshifted H0 X (so that no large shift enters
 // the working-precision data) and sigma is applied here in FP64.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -81,49 +83,58 @@ __device__ void block_sum_vec(double (&v)[NV], double* sh /* >= 32 * NV */) {
 
 }  // namespace
 
-template <typename T>
-__global__ void __launch_bounds__(1024) line_search_kernel(const double2* __restrict__ Cg, int N, double sigma,
-                                                           int have_d, double tol, OmmScalars* sc,
-                                                           cx_t<T>* __restrict__ M1, cx_t<T>* __restrict__ M2) {
-  __shared__ double sh[32 * 12];
-  __shared__ double t_sh;
-  const int ld = 4 * N;
-  auto at = [&](int r, int c) { return Cg[(size_t)r * ld + c]; };
-  // shifted blocks as functions of (i, j)
-  auto A = [&](int i, int j) { return at(i, j); };
-  auto Bm = [&](int i, int j) {
-    double2 a = at(i, N + j), b = at(N + i, j);
+// The fused Gram's blocks, shifted by sigma where H enters, as functions of (i, j).
+struct LsBlocks {
+  const double2* Cg;
+  int N, ld;
+  double sigma;
+  __device__ double2 at(int r, int c) const { return Cg[(size_t)r * ld + c]; }
+  __device__ double2 A(int i, int j) const { return at(i, j); }
+  __device__ double2 B(int i, int j) const {
+    const double2 a = at(i, N + j), b = at(N + i, j);
     return make_double2(a.x + b.x, a.y + b.y);
-  };
-  auto Cm = [&](int i, int j) { return at(N + i, N + j); };
-  auto AH = [&](int i, int j) {
-    double2 h = at(i, 2 * N + j), s = at(i, j);
+  }
+  __device__ double2 Cm(int i, int j) const { return at(N + i, N + j); }
+  __device__ double2 AH(int i, int j) const {
+    const double2 h = at(i, 2 * N + j), s = at(i, j);
     return make_double2(h.x - sigma * s.x, h.y - sigma * s.y);
-  };
-  auto BH = [&](int i, int j) {
-    double2 h1 = at(i, 3 * N + j), h2 = at(N + i, 2 * N + j);
-    double2 s = Bm(i, j);
+  }
+  __device__ double2 BH(int i, int j) const {
+    const double2 h1 = at(i, 3 * N + j), h2 = at(N + i, 2 * N + j), s = B(i, j);
     return make_double2(h1.x + h2.x - sigma * s.x, h1.y + h2.y - sigma * s.y);
-  };
-  auto CH = [&](int i, int j) {
-    double2 h = at(N + i, 3 * N + j), s = at(N + i, N + j);
+  }
+  __device__ double2 CH(int i, int j) const {
+    const double2 h = at(N + i, 3 * N + j), s = at(N + i, N + j);
     return make_double2(h.x - sigma * s.x, h.y - sigma * s.y);
-  };
+  }
+};
+
+// Line search in three launches (the traces are O(N^2) FP64 work that one CTA would run on
+// one SM): ls_traces, one CTA per row i, sums row i's terms of the 12 traces
+//   v: 0 trAH, 1 trBH, 2 trCH, 3 tr(A AH), 4 tr(A BH), 5 tr(B AH), 6 tr(A CH), 7 tr(B BH),
+//      8 tr(C AH), 9 tr(B CH), 10 tr(C BH), 11 tr(C CH)
+// into work[i][12]; ls_solve adds the rows in order, forms the quartic and finds its
+// minimiser; ls_matrices forms M1, M2 at the chosen step.
+constexpr int LS_NV = 12;
+
+__global__ void __launch_bounds__(128) ls_traces_kernel(LsBlocks g, int have_d, double* __restrict__ work) {
+  __shared__ double sh[32 * LS_NV];
+  const int i = blockIdx.x, N = g.N;
   auto rmul = [](double2 p, double2 q) { return p.x * q.x - p.y * q.y; };  // Re(p q)
-  // v: 0 trAH, 1 trBH, 2 trCH, 3 tr(A AH), 4 tr(A BH), 5 tr(B AH), 6 tr(A CH), 7 tr(B BH),
-  //    8 tr(C AH), 9 tr(B CH), 10 tr(C BH), 11 tr(C CH)
-  double v[12];
+  double v[LS_NV];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) v[q] = 0.0;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx % N;
-    const double2 a_ij = A(i, j), ah_ji = AH(j, i);
+  for (int q = 0; q < LS_NV; ++q) v[q] = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double2 a_ij = g.A(i, j), ah_ji = g.AH(j, i);
     if (i == j) v[0] += ah_ji.x;
     v[3] += rmul(a_ij, ah_ji);
     if (have_d) {
-      const double2 b_ij = Bm(i, j), c_ij = Cm(i, j);
-      const double2 bh_ji = BH(j, i), ch_ji = CH(j, i);
-      if (i == j) { v[1] += bh_ji.x; v[2] += ch_ji.x; }
+      const double2 b_ij = g.B(i, j), c_ij = g.Cm(i, j);
+      const double2 bh_ji = g.BH(j, i), ch_ji = g.CH(j, i);
+      if (i == j) {
+        v[1] += bh_ji.x;
+        v[2] += ch_ji.x;
+      }
       v[4] += rmul(a_ij, bh_ji);
       v[5] += rmul(b_ij, ah_ji);
       v[6] += rmul(a_ij, ch_ji);
@@ -134,55 +145,71 @@ __global__ void __launch_bounds__(1024) line_search_kernel(const double2* __rest
       v[11] += rmul(c_ij, ch_ji);
     }
   }
-  block_sum_vec<12>(v, sh);
-  if (threadIdx.x == 0) {
-    double c[5];
-    c[0] = v[0] - 0.5 * v[3];
-    c[1] = v[1] - 0.5 * (v[4] + v[5]);
-    c[2] = v[2] - 0.5 * (v[6] + v[7] + v[8]);
-    c[3] = -0.5 * (v[9] + v[10]);
-    c[4] = -0.5 * v[11];
-    double t = 0.0;
-    int bad = 0;
-    if (have_d) {
-      if (!(c[4] > 0.0)) {
-        bad = 1;
-      } else {
-        double a[4] = {c[1], 2.0 * c[2], 3.0 * c[3], 4.0 * c[4]};
-        double r[3];
-        const int nr = cubic_real_roots(a, r);
-        double best = quartic(c, r[0]);
-        t = r[0];
-        for (int i = 1; i < nr; ++i) {
-          const double e = quartic(c, r[i]);
-          const double tie = 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(best));
-          if (e < best - tie || (fabs(e - best) <= tie && fabs(r[i]) < fabs(t))) {
-            best = e;
-            t = r[i];
-          }
+  block_sum_vec<LS_NV>(v, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < LS_NV; ++q) work[(size_t)i * LS_NV + q] = v[q];
+}
+
+__global__ void ls_solve_kernel(int N, int have_d, double tol, const double* __restrict__ work, OmmScalars* sc) {
+  __shared__ double v[LS_NV];
+  if (threadIdx.x < LS_NV) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += work[(size_t)i * LS_NV + threadIdx.x];   // rows in order
+    v[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double c[5];
+  c[0] = v[0] - 0.5 * v[3];
+  c[1] = v[1] - 0.5 * (v[4] + v[5]);
+  c[2] = v[2] - 0.5 * (v[6] + v[7] + v[8]);
+  c[3] = -0.5 * (v[9] + v[10]);
+  c[4] = -0.5 * v[11];
+  double t = 0.0;
+  int bad = 0;
+  if (have_d) {
+    if (!(c[4] > 0.0)) {
+      bad = 1;
+    } else {
+      double a[4] = {c[1], 2.0 * c[2], 3.0 * c[3], 4.0 * c[4]};
+      double r[3];
+      const int nr = cubic_real_roots(a, r);
+      double best = quartic(c, r[0]);
+      t = r[0];
+      for (int k = 1; k < nr; ++k) {
+        const double e = quartic(c, r[k]);
+        const double tie = 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(best));
+        if (e < best - tie || (fabs(e - best) <= tie && fabs(r[k]) < fabs(t))) {
+          best = e;
+          t = r[k];
         }
       }
     }
-    for (int q = 0; q < 5; ++q) sc->c[q] = c[q];
-    sc->t = t;
-    sc->t_c = make_double2(t, 0.0);
-    sc->one_c = make_double2(1.0, 0.0);
-    sc->E0 = c[0];
-    sc->E1 = quartic(c, t);
-    sc->bad = bad;
-    sc->converged = fabs(sc->E1 - sc->E0) <= tol * fabs(sc->E1);
-    t_sh = t;
   }
-  __syncthreads();
-  const double t = t_sh;
-  // Grams of X + tD (unshifted K0), then M1 = -(K0 + 2 sigma (I - S)), M2 = -S
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+  for (int q = 0; q < 5; ++q) sc->c[q] = c[q];
+  sc->t = t;
+  sc->t_c = make_double2(t, 0.0);
+  sc->one_c = make_double2(1.0, 0.0);
+  sc->E0 = c[0];
+  sc->E1 = quartic(c, t);
+  sc->bad = bad;
+  sc->converged = fabs(sc->E1 - sc->E0) <= tol * fabs(sc->E1);
+}
+
+// Grams of X + tD (unshifted K0), then M1 = -(K0 + 2 sigma (I - S)), M2 = -S
+template <typename T>
+__global__ void ls_matrices_kernel(LsBlocks g, int have_d, const OmmScalars* __restrict__ sc, cx_t<T>* __restrict__ M1,
+                                   cx_t<T>* __restrict__ M2) {
+  const int N = g.N;
+  const double t = sc->t, sigma = g.sigma;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N; idx += gridDim.x * blockDim.x) {
     const int i = idx / N, j = idx % N;
-    double2 S = A(i, j);
-    double2 K0 = at(i, 2 * N + j);
+    double2 S = g.A(i, j);
+    double2 K0 = g.at(i, 2 * N + j);
     if (have_d) {
-      const double2 b = Bm(i, j), cc = Cm(i, j);
-      const double2 h1 = at(i, 3 * N + j), h2 = at(N + i, 2 * N + j), hd = at(N + i, 3 * N + j);
+      const double2 b = g.B(i, j), cc = g.Cm(i, j);
+      const double2 h1 = g.at(i, 3 * N + j), h2 = g.at(N + i, 2 * N + j), hd = g.at(N + i, 3 * N + j);
       S.x += t * b.x + t * t * cc.x;
       S.y += t * b.y + t * t * cc.y;
       K0.x += t * (h1.x + h2.x) + t * t * hd.x;
@@ -197,11 +224,16 @@ __global__ void __launch_bounds__(1024) line_search_kernel(const double2* __rest
 }
 
 cudaError_t launch_line_search(bool dbl, const double2* C, int N, double sigma, int have_d, double tol,
-                               OmmScalars* sc, void* M1, void* M2, cudaStream_t st) {
+                               OmmScalars* sc, void* M1, void* M2, double* work, cudaStream_t st) {
+  if (N < 1 || !work) return cudaErrorInvalidValue;
+  const LsBlocks g{C, N, 4 * N, sigma};
+  ls_traces_kernel<<<N, 128, 0, st>>>(g, have_d, work);
+  ls_solve_kernel<<<1, 32, 0, st>>>(N, have_d, tol, work, sc);
+  const int blocks = std::min((N * N + 255) / 256, 1024);
   if (dbl)
-    line_search_kernel<double><<<1, 1024, 0, st>>>(C, N, sigma, have_d, tol, sc, (double2*)M1, (double2*)M2);
+    ls_matrices_kernel<double><<<blocks, 256, 0, st>>>(g, have_d, sc, (double2*)M1, (double2*)M2);
   else
-    line_search_kernel<float><<<1, 1024, 0, st>>>(C, N, sigma, have_d, tol, sc, (float2*)M1, (float2*)M2);
+    ls_matrices_kernel<float><<<blocks, 256, 0, st>>>(g, have_d, sc, (float2*)M1, (float2*)M2);
   return cudaGetLastError();
 }
 

@@ -75,8 +75,9 @@ struct OmmScalars {
 // quartic coefficients with H = H0 - sigma, exact line search, energies; then the Grams of
 // X + tD (S, K0) and the update matrices M1 = -(K0 + 2 sigma (I - S)), M2 = -S in the
 // working precision for the next gradient.  If have_d == 0 only E0 and M1, M2 at t = 0.
+// work: N x 12 doubles of device scratch (the per-row partial traces).
 cudaError_t launch_line_search(bool dbl, const double2* C, int N, double sigma, int have_d, double tol,
-                               OmmScalars* sc, void* M1, void* M2, cudaStream_t st);
+                               OmmScalars* sc, void* M1, void* M2, double* work, cudaStream_t st);
 // beta = (gg - gdot) / ggp (Polak-Ribiere); first == 1 sets beta = 0.
 // M = scale * C (N x N FP64 Gram with row stride ldc) in the working precision
 cudaError_t launch_gram_to_matrix(bool dbl, const double2* C, int ldc, int N, double scale, void* M, cudaStream_t st);

@@ -22,6 +22,20 @@ struct GridCfg {
   static constexpr size_t smem = sizeof(cx_t<T>) * (LY::SIZE + M);
 };
 
+// The grid function x into the padded shared-memory layout with cp.async (global to shared
+// memory without a register round trip, every copy of the thread in flight at once); the
+// caller's __syncthreads follows.
+template <typename T, int M, int D>
+__device__ __forceinline__ void load_grid_async(cx_t<T>* s, const cx_t<T>* __restrict__ x) {
+  using G = GridCfg<T, M, D>;
+  using LY = typename G::LY;
+  for (int i = threadIdx.x; i < G::N; i += G::NT) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s + LY::at_flat(i));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(x + i), "n"(sizeof(cx_t<T>)) : "memory");
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 template <typename T, int M, int D>
 __global__ void __launch_bounds__(GridCfg<T, M, D>::NT)
 happly_kernel(const cx_t<T>* __restrict__ X, cx_t<T>* __restrict__ Y, const T* __restrict__ V,
@@ -38,6 +52,7 @@ happly_kernel(const cx_t<T>* __restrict__ X, cx_t<T>* __restrict__ Y, const T* _
   if (active && !active[col]) return;
   const C* x = X + (size_t)col * G::N;
   for (int i = threadIdx.x; i < M; i += NT) t[i] = tw[i];
+  // (plain loads: with cp.async the H-apply measured slower, its epilogue re-reads x)
   for (int i = threadIdx.x; i < G::N; i += NT) s[LY::at_flat(i)] = x[i];
   __syncthreads();
   fft::transform<-1, LY, G::MZ, NT>(s, t, t, t);
@@ -84,7 +99,7 @@ greenq_kernel(const cx_t<T>* __restrict__ B, cx_t<T>* __restrict__ Out, const cx
   const C* b = B + (size_t)col * G::N;
   for (int i = threadIdx.x; i < M; i += NT) t[i] = tw[i];
   for (int i = threadIdx.x; i < nq; i += NT) qs[i] = q[(size_t)g * nq + i];
-  for (int i = threadIdx.x; i < G::N; i += NT) s[LY::at_flat(i)] = b[i];
+  load_grid_async<T, M, D>(s, b);
   __syncthreads();
   fft::transform<-1, LY, G::MZ, NT>(s, t, t, t);
   const C* gh = ghat + (size_t)g * G::N;

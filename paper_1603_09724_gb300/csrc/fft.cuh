@@ -147,9 +147,16 @@ template <int MX, int MY, int MZ> struct Lines<Layout<MX, MY, MZ>, 2> {  // alon
   __device__ __forceinline__ static int base(int l) { return (l / MX) * LY::PX + (l % MX); }
 };
 
-// One in-place Stockham pass (radix R, NS = product of earlier radices).
-template <int R, int NS, int SGN, class LN, int NT, typename C>
-__device__ __forceinline__ void pass(C* s, const C* tw) {
+// Identity: the element-wise operation a pass applies to its inputs by default.
+struct NoPre {
+  template <typename C> __device__ __forceinline__ C operator()(C v, int, int) const { return v; }
+};
+
+// One in-place Stockham pass (radix R, NS = product of earlier radices).  pre(v, l, pos)
+// is applied to every input as it is loaded (line l, position pos along the axis), so a
+// point-wise multiplier can ride on the first pass of a transform.
+template <int R, int NS, int SGN, class LN, int NT, typename C, class F = NoPre>
+__device__ __forceinline__ void pass(C* s, const C* tw, F pre = F()) {
   constexpr int M = LN::M;
   constexpr int NBL = M / R;
   constexpr int NB = LN::NL * NBL;
@@ -162,7 +169,7 @@ __device__ __forceinline__ void pass(C* s, const C* tw) {
       const int l = b % LN::NL, j = b / LN::NL;
       const C* base = s + LN::base(l);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[p][r] = base[(j + r * NBL) * LN::ESTR];
+      for (int r = 0; r < R; ++r) v[p][r] = pre(base[(j + r * NBL) * LN::ESTR], l, j + r * NBL);
       if constexpr (NS > 1) {
         const int jm = j % NS;
         constexpr int STEP = M / (NS * R);
@@ -191,25 +198,33 @@ __device__ __forceinline__ void pass(C* s, const C* tw) {
   __syncthreads();
 }
 
-// Full unnormalised DFT along one axis (SGN = -1 forward, +1 inverse).
-template <int SGN, class LN, int NT, typename C> __device__ __forceinline__ void axis(C* s, const C* tw) {
+// Full unnormalised DFT along one axis (SGN = -1 forward, +1 inverse); pre rides on the
+// first pass.
+template <int SGN, class LN, int NT, typename C, class F = NoPre>
+__device__ __forceinline__ void axis(C* s, const C* tw, F pre = F()) {
   using P = Plan<LN::M>;
-  pass<P::r0, 1, SGN, LN, NT>(s, tw);
+  pass<P::r0, 1, SGN, LN, NT>(s, tw, pre);
   if constexpr (P::np > 1) pass<P::r1, P::r0, SGN, LN, NT>(s, tw);
   if constexpr (P::np > 2) pass<P::r2, P::r0 * P::r1, SGN, LN, NT>(s, tw);
   if constexpr (P::np > 3) pass<P::r3, P::r0 * P::r1 * P::r2, SGN, LN, NT>(s, tw);
 }
 
-// Forward / inverse transform of the whole grid (all axes).
-template <int SGN, class LY, int MZ, int NT, typename C>
-__device__ __forceinline__ void transform(C* s, const C* twx, const C* twy, const C* twz) {
+// Forward / inverse transform of the whole grid (all axes).  pre rides on the first pass
+// of the first axis (x forward; z, else y, inverse): pre(v, l, pos) with that axis's line
+// index l and position pos.
+template <int SGN, class LY, int MZ, int NT, typename C, class F = NoPre>
+__device__ __forceinline__ void transform(C* s, const C* twx, const C* twy, const C* twz, F pre = F()) {
   if constexpr (SGN < 0) {
-    axis<SGN, Lines<LY, 0>, NT>(s, twx);
+    axis<SGN, Lines<LY, 0>, NT>(s, twx, pre);
     axis<SGN, Lines<LY, 1>, NT>(s, twy);
     if constexpr (MZ > 1) axis<SGN, Lines<LY, 2>, NT>(s, twz);
   } else {
-    if constexpr (MZ > 1) axis<SGN, Lines<LY, 2>, NT>(s, twz);
-    axis<SGN, Lines<LY, 1>, NT>(s, twy);
+    if constexpr (MZ > 1) {
+      axis<SGN, Lines<LY, 2>, NT>(s, twz, pre);
+      axis<SGN, Lines<LY, 1>, NT>(s, twy);
+    } else {
+      axis<SGN, Lines<LY, 1>, NT>(s, twy, pre);
+    }
     axis<SGN, Lines<LY, 0>, NT>(s, twx);
   }
 }

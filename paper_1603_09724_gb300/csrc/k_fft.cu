@@ -22,6 +22,35 @@ struct GridCfg {
   static constexpr size_t smem = sizeof(cx_t<T>) * (LY::SIZE + M);
 };
 
+// Point-wise multipliers applied as the first pass of the inverse transform loads its
+// inputs (fft::transform's pre; that pass runs along y in 2D, z in 3D): the grid point of
+// input (line l, position pos) is x = l % M and y = pos (2D), or y = l / M and z = pos (3D).
+template <int M, int D>
+__device__ __forceinline__ int flat_of_inverse_line(int l, int pos) {
+  return D == 3 ? pos * M * M + l : pos * M + l;
+}
+
+// the kinetic symbol c |k|^2 (the H-apply)
+template <typename T, int M, int D>
+struct KineticPre {
+  T kc;
+  __device__ __forceinline__ cx_t<T> operator()(cx_t<T> v, int l, int pos) const {
+    const int kx = fft::signed_k(l % M, M);
+    const int ky = fft::signed_k(D == 3 ? l / M : pos, M);
+    const int kz = D == 3 ? fft::signed_k(pos, M) : 0;
+    return cscale(v, kc * (T)(kx * kx + ky * ky + kz * kz));
+  }
+};
+
+// the Green symbol of the column's group (the Green kernel)
+template <typename T, int M, int D>
+struct GreenPre {
+  const cx_t<T>* gh;
+  __device__ __forceinline__ cx_t<T> operator()(cx_t<T> v, int l, int pos) const {
+    return cmul(v, gh[flat_of_inverse_line<M, D>(l, pos)]);
+  }
+};
+
 // The grid function x into the padded shared-memory layout with cp.async (global to shared
 // memory without a register round trip, every copy of the thread in flight at once); the
 // caller's __syncthreads follows.
@@ -56,16 +85,7 @@ happly_kernel(const cx_t<T>* __restrict__ X, cx_t<T>* __restrict__ Y, const T* _
   for (int i = threadIdx.x; i < G::N; i += NT) s[LY::at_flat(i)] = x[i];
   __syncthreads();
   fft::transform<-1, LY, G::MZ, NT>(s, t, t, t);
-  const T kc = (T)kin_over_n;
-  for (int i = threadIdx.x; i < G::N; i += NT) {
-    const int ix = i % M, iy = (i / M) % M, iz = i / (M * M);
-    const int kx = fft::signed_k(ix, M), ky = fft::signed_k(iy, M), kz = (D == 3) ? fft::signed_k(iz, M) : 0;
-    const T k2 = (T)(kx * kx + ky * ky + kz * kz);
-    const int a = LY::at_flat(i);
-    s[a] = cscale(s[a], kc * k2);
-  }
-  __syncthreads();
-  fft::transform<+1, LY, G::MZ, NT>(s, t, t, t);
+  fft::transform<+1, LY, G::MZ, NT>(s, t, t, t, KineticPre<T, M, D>{(T)kin_over_n});
   const double2 sh = shifts[col / cols_per_group];
   const T sr = (T)sh.x, si = (T)sh.y;
   C* y = Y + (size_t)col * G::N;
@@ -102,13 +122,7 @@ greenq_kernel(const cx_t<T>* __restrict__ B, cx_t<T>* __restrict__ Out, const cx
   load_grid_async<T, M, D>(s, b);
   __syncthreads();
   fft::transform<-1, LY, G::MZ, NT>(s, t, t, t);
-  const C* gh = ghat + (size_t)g * G::N;
-  for (int i = threadIdx.x; i < G::N; i += NT) {
-    const int a = LY::at_flat(i);
-    s[a] = cmul(s[a], gh[i]);
-  }
-  __syncthreads();
-  fft::transform<+1, LY, G::MZ, NT>(s, t, t, t);
+  fft::transform<+1, LY, G::MZ, NT>(s, t, t, t, GreenPre<T, M, D>{ghat + (size_t)g * G::N});
   C* o = Out + (size_t)col * G::N;
   if constexpr (D == 2 && NT % M == 0 && M % (NT / M) == 0) {
     if (nq == 9) {

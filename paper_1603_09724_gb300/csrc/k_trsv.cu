@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
 #pragma unroll
       for (int t = 0; t < LNB; ++t) {
         const int i = ibs[j * LNB + t];
-        if (i >= 0) acc = cfma(Fbs[j * LNB + t], y[i * LDY], acc);
+        if (i < 0) break;   // the -1 padding trails: a halo row couples to few leaf unknowns
+        acc = cfma(Fbs[j * LNB + t], y[i * LDY], acc);
       }
       u[(size_t)(uoff + j) * a.S + s0 + tid] = acc;
     }
@@ -630,7 +631,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(TrsvArgs a, LeafArgs la, const
 #pragma unroll
         for (int t = 0; t < LNB; ++t) {   // -1 entries trail: same order as a breaking loop
           const int j = isb[i * LNB + t];
-          if (j >= 0) acc = cfma(Fsb[i * LNB + t], hs[j * LHS + lane], acc);
+          if (j < 0) break;   // interior leaf unknowns have no halo couplings at all
+          acc = cfma(Fsb[i * LNB + t], hs[j * LHS + lane], acc);
         }
         if (live[cb + lane]) ys[i * LDY + cb + lane] = acc;
       }

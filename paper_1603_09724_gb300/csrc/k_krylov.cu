@@ -4,6 +4,9 @@
 // on the small Hessenberg matrix, and the preconditioned basis Z kept for the update
 // x += Z y.  One CTA per system for the vector work; one thread per system for the
 // small (m <= 16) dense work.  System s = p * N + c.
+#include <cstdint>
+#include <initializer_list>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -90,12 +93,76 @@ __global__ void __launch_bounds__(KT) krylov_init_kernel(KrylovDims d, const cx_
   }
 }
 
+// The same cycle start for complex64 with an even grid and 16-byte aligned vectors: two
+// entries per float4 load / store.
+__global__ void __launch_bounds__(KT) krylov_init_c64x2_kernel(KrylovDims d, const float4* __restrict__ b,
+                                                               const float4* __restrict__ Hx,
+                                                               const double2* __restrict__ shifts,
+                                                               float4* __restrict__ V0, float4* __restrict__ x,
+                                                               double* __restrict__ beta, double2* __restrict__ g,
+                                                               double* __restrict__ bnorm, int* __restrict__ active,
+                                                               double rtol, int fixed, int first) {
+  __shared__ double sh[2 * (KT / 32)];
+  const int s = blockIdx.x;
+  const int c = s % d.N, p = s / d.N;
+  const size_t n2 = d.n / 2;
+  const float4* bc = b + (size_t)c * n2;
+  const float4* hx = first ? Hx + (size_t)c * n2 : Hx + (size_t)s * n2;
+  const double2 sh_p = first ? shifts[p] : make_double2(0.0, 0.0);
+  const float sr = (float)sh_p.x, si = (float)sh_p.y;
+  auto resid = [&](float2 bi, float2 hi) {   // b - A x (first: b - (H0 b - shift b))
+    float2 r = csub(bi, hi);
+    if (first) {
+      r.x += sr * bi.x - si * bi.y;
+      r.y += sr * bi.y + si * bi.x;
+    }
+    return r;
+  };
+  float a0 = 0, a1 = 0;
+  for (size_t i = threadIdx.x; i < n2; i += KT) {
+    const float4 bv = bc[i], hv = hx[i];
+    const float2 b0 = make_float2(bv.x, bv.y), b1 = make_float2(bv.z, bv.w);
+    const float2 r0 = resid(b0, make_float2(hv.x, hv.y)), r1 = resid(b1, make_float2(hv.z, hv.w));
+    if (first) x[(size_t)s * n2 + i] = bv;
+    a0 += r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y;
+    a1 += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
+  }
+  double acc[2] = {(double)a0, (double)a1};
+  block_reduce<2>(acc, sh);
+  const double bt = sqrt(acc[0]);
+  const double bn = first ? sqrt(acc[1]) : bnorm[s];
+  const float inv = bt > 0.0 ? (float)(1.0 / bt) : 0.f;
+  for (size_t i = threadIdx.x; i < n2; i += KT) {
+    const float4 bv = bc[i], hv = hx[i];
+    const float2 r0 = resid(make_float2(bv.x, bv.y), make_float2(hv.x, hv.y));
+    const float2 r1 = resid(make_float2(bv.z, bv.w), make_float2(hv.z, hv.w));
+    V0[(size_t)s * n2 + i] = make_float4(r0.x * inv, r0.y * inv, r1.x * inv, r1.y * inv);
+  }
+  if (threadIdx.x == 0) {
+    beta[s] = bt;
+    if (first) bnorm[s] = bn;
+    for (int k = 0; k <= d.m; ++k) g[(size_t)s * (KMAX + 1) + k] = make_double2(k == 0 ? bt : 0.0, 0.0);
+    const double rel = bn > 0.0 ? bt / bn : 0.0;
+    active[s] = (bt > 0.0) && (fixed || rel > rtol);
+  }
+}
+
+static bool pairs_ok(const KrylovDims& d, std::initializer_list<const void*> ptrs) {
+  if (d.n % 2) return false;
+  for (const void* q : ptrs)
+    if (q && (uintptr_t)q % 16) return false;
+  return true;
+}
+
 cudaError_t launch_krylov_init0(bool dbl, KrylovDims d, const void* b, const void* Hb, const double2* shifts, void* V0,
                                 void* x, double* beta, double2* g, double* bnorm, int* active, double rtol, int fixed,
                                 cudaStream_t st) {
   if (dbl)
     krylov_init_kernel<double><<<d.S, KT, 0, st>>>(d, (const double2*)b, (const double2*)Hb, shifts, (double2*)V0,
                                                    (double2*)x, beta, g, bnorm, active, rtol, fixed, 1);
+  else if (pairs_ok(d, {b, Hb, V0, x}))
+    krylov_init_c64x2_kernel<<<d.S, KT, 0, st>>>(d, (const float4*)b, (const float4*)Hb, shifts, (float4*)V0,
+                                                 (float4*)x, beta, g, bnorm, active, rtol, fixed, 1);
   else
     krylov_init_kernel<float><<<d.S, KT, 0, st>>>(d, (const float2*)b, (const float2*)Hb, shifts, (float2*)V0,
                                                   (float2*)x, beta, g, bnorm, active, rtol, fixed, 1);
@@ -109,6 +176,9 @@ cudaError_t launch_krylov_restart(bool dbl, KrylovDims d, const void* b, const v
     krylov_init_kernel<double><<<d.S, KT, 0, st>>>(d, (const double2*)b, (const double2*)Ax, nullptr,
                                                    (double2*)V0, nullptr, beta, g, (double*)bnorm, active, rtol,
                                                    fixed, 0);
+  else if (pairs_ok(d, {b, Ax, V0}))
+    krylov_init_c64x2_kernel<<<d.S, KT, 0, st>>>(d, (const float4*)b, (const float4*)Ax, nullptr, (float4*)V0,
+                                                 nullptr, beta, g, (double*)bnorm, active, rtol, fixed, 0);
   else
     krylov_init_kernel<float><<<d.S, KT, 0, st>>>(d, (const float2*)b, (const float2*)Ax, nullptr,
                                                   (float2*)V0, nullptr, beta, g, (double*)bnorm, active, rtol, fixed,

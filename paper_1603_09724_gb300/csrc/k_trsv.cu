@@ -128,6 +128,10 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
   if (r0 >= M) return;   // a split past the node's last row (uniform over the CTA)
   const C* W = factor + (size_t)p * a.factor_size + (FWD ? a.node_wf[node] : a.node_wb[node]);
   const int tid = threadIdx.x;
+  // W_f's top block L_SS^-1 is lower and W_b's left block U_SS^-1 upper triangular: the
+  // products of this row block run over the k range [klo, khi) that can hold nonzeros
+  const int klo = FWD ? 0 : r0;
+  const int khi = (FWD && r0 + RBV <= ns) ? min(K, r0 + RBV) : K;
   // W tiles: each thread holds WPT elements of the next tile in registers while the
   // current tile is consumed from shared memory (one barrier per k step).  The first tile
   // is loaded before the wait on the previous launch (GD): the factor is not written there.
@@ -139,10 +143,10 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
       const int idx = tid + q * NTH;
       const int kk = idx % KT, rr = idx / KT;   // k fastest: coalesced rows of W
       const int r = r0 + rr, k = k0 + kk;
-      wreg[q] = (r < M && k < K) ? W[(size_t)r * K + k] : mk<C>(0, 0);
+      wreg[q] = (r < M && k < khi) ? W[(size_t)r * K + k] : mk<C>(0, 0);
     }
   };
-  load_w(0);
+  load_w(klo);
   if (GD) {
     griddep_wait();
     griddep_launch();
@@ -151,15 +155,16 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
   // independent loads in flight per thread
   constexpr int FB = 8;
   const int boff = a.node_boff[node];
-  for (int base = tid; base < K * RT; base += FB * NTH) {
+  const int Kr = khi - klo;   // staged rows klo .. khi-1 of the block (Bs keeps absolute rows)
+  for (int base = tid; base < Kr * RT; base += FB * NTH) {
     C v[FB];
 #pragma unroll
     for (int q = 0; q < FB; ++q) {
       const int idx = base + q * NTH;
-      const int i = idx % K, cc = idx / K;
+      const int i = klo + idx % Kr, cc = idx / Kr;
       const int c = c0 + cc;
       v[q] = mk<C>(0, 0);
-      if (idx < K * RT && c < a.N) {
+      if (idx < Kr * RT && c < a.N) {
         const size_t s = (size_t)p * a.N + c;
         if (FWD) {   // assembled by assemble_kernel into xnd
           if (!active || active[s]) v[q] = __ldcg(xnd + s * a.n + off + i);
@@ -171,7 +176,7 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
 #pragma unroll
     for (int q = 0; q < FB; ++q) {
       const int idx = base + q * NTH;
-      if (idx < K * RT) Bs[(idx % K) * RT + idx / K] = v[q];
+      if (idx < Kr * RT) Bs[(klo + idx % Kr) * RT + idx / Kr] = v[q];
     }
   }
   __syncthreads();
@@ -183,15 +188,15 @@ __device__ __forceinline__ void gemm_tile(const TrsvArgs& a, const int* __restri
 #pragma unroll
     for (int j = 0; j < TC; ++j) acc[i][j] = mk<C>(0, 0);
   int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += KT, buf ^= 1) {
+  for (int k0 = klo; k0 < khi; k0 += KT, buf ^= 1) {
 #pragma unroll
     for (int q = 0; q < WPT; ++q) {
       const int idx = tid + q * NTH;
       As[buf][idx % KT][idx / KT] = wreg[q];
     }
     __syncthreads();
-    if (k0 + KT < K) load_w(k0 + KT);
-    const int kmax = min(KT, K - k0);
+    if (k0 + KT < khi) load_w(k0 + KT);
+    const int kmax = min(KT, khi - k0);
     for (int kk = 0; kk < kmax; ++kk) {
       C av[4], bv[TC];
 #pragma unroll
@@ -296,8 +301,13 @@ __device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __res
   // previous launch (GD): the factor is not written there
   const int w = tid >> 5, lane = tid & 31;
   const int rg = lane / CGS, cg = lane % CGS;
-  const int kw = (K + KS - 1) / KS;
-  const int kb = w * kw, ke = min(K, kb + kw);
+  // only the k range [klo, khi) of this row block can hold nonzeros (L_SS^-1 lower,
+  // U_SS^-1 upper triangular); the warps split that range
+  const int klo = FWD ? 0 : r0;
+  const int khi = (FWD && r0 + RBS <= ns) ? min(K, r0 + RBS) : K;
+  const int Kr = khi - klo;
+  const int kw = (Kr + KS - 1) / KS;
+  const int kb = klo + w * kw, ke = min(khi, kb + kw);
   C* Ws = Wall + (size_t)w * SK_WK * (RBS + 1);
   constexpr int WPL = RBS * SK_WK / 32;   // W values per lane per chunk
   C wv[WPL];
@@ -315,18 +325,19 @@ __device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __res
     griddep_wait();
     griddep_launch();
   }
-  // ---- right-hand-side block (i fastest: contiguous runs of one system's column)
+  // ---- right-hand-side block (i fastest: contiguous runs of one system's column), rows
+  // klo .. khi-1 (Bs keeps absolute rows)
   constexpr int FB = 8;
   const int boff = a.node_boff[node];
-  for (int base = tid; base < K * RT; base += FB * NTH) {
+  for (int base = tid; base < Kr * RT; base += FB * NTH) {
     C v[FB];
 #pragma unroll
     for (int q = 0; q < FB; ++q) {
       const int idx = base + q * NTH;
-      const int i = idx % K, cc = idx / K;
+      const int i = klo + idx % Kr, cc = idx / Kr;
       const int c = c0 + cc;
       v[q] = mk<C>(0, 0);
-      if (idx < K * RT && c < a.N) {
+      if (idx < Kr * RT && c < a.N) {
         const size_t s = (size_t)p * a.N + c;
         if (FWD) {
           if (!active || active[s]) v[q] = __ldcg(xnd + s * a.n + off + i);
@@ -338,7 +349,7 @@ __device__ __forceinline__ void gemm_sk_tile(const TrsvArgs& a, const int* __res
 #pragma unroll
     for (int q = 0; q < FB; ++q) {
       const int idx = base + q * NTH;
-      if (idx < K * RT) Bs[(idx % K) * RT + idx / K] = v[q];
+      if (idx < Kr * RT) Bs[(klo + idx % Kr) * RT + idx / Kr] = v[q];
     }
   }
   __syncthreads();

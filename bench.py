@@ -513,7 +513,7 @@ def roofline_record(prof, dom, wl, peaks, sm_mhz, gram_tensor, apps):
     """Roofline of the dominant kernel class `dom` from the untimed per-class profile.
 
     HBM-bound classes: the class's algorithmic bytes (the library's count: H-apply 2v plus V,
-    Green 2v plus the symbol tables, CGS2 (2(k+1)+3) vectors, triangular solves 4 per
+    Green 2v plus the symbol tables, CGS2 k+3 vectors (basis and w read once, the new vector written), triangular solves 4 per
     unknown and active system plus the factor) / its CUDA-event time, against the measured
     copy bandwidth.  The Gram class (it dominates only when the preconditioner is cheap,
     e.g. gTPA) is compute-bound: 48 n N^2 algorithmic real flops per fused Gram [X D]^*
@@ -546,7 +546,7 @@ def roofline_record(prof, dom, wl, peaks, sm_mhz, gram_tensor, apps):
         "trsv_leaf": "per application: 4 x n_leaf x 8 B per active system + the leaf factor values of every pole once",
         "happly": "2 x n x 8 B per column (X in, Y out) + V",
         "greenq": "2 x n x 8 B per column + the Green symbol of each pole",
-        "orth": "(2(k+1) + 3) x n x 8 B per active system at Arnoldi step k",
+        "orth": "(k + 3) x n x 8 B per active system at Arnoldi step k (V_0..V_k and w read once, V_k+1 written)",
     }.get(dom, "the library's algorithmic byte count")
     tr = TRAFFIC_PER_CALL.get((getattr(wl, "name", None), N, dom))
     rec = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,

@@ -685,8 +685,11 @@ omm_status pole_solve(omm_ctx* h, const void* R, void* out, double sign) {
       ++steps_run;
       OMM_TRY(inner_apply(h, P, N, Vk(k), Zk(k), h->active, h->tv));
       OMM_TRY(happly(h, Zk(k), h->wv, d.S, h->shifts, N, h->active));
-      PROF(PC_ORTH, (2.0 * (k + 1) + 3.0) * live_cols(h, d.S, h->active) * h->n * h->csz, 1,
-           cuda_status(launch_krylov_orth(h->dbl, d, k, h->Vb, h->wv, h->Hh, h->active, h->st), "orth"));
+      // algorithmic: the k + 1 basis vectors and w read once, V_{k+1} written; the kernels
+      // stream the basis and w once per sweep, three times
+      PROF2(PC_ORTH, (k + 3.0) * live_cols(h, d.S, h->active) * h->n * h->csz,
+            (3.0 * k + 7.0) * live_cols(h, d.S, h->active) * h->n * h->csz, 1,
+            cuda_status(launch_krylov_orth(h->dbl, d, k, h->Vb, h->wv, h->Hh, h->active, h->st), "orth"));
       OMM_TRY(cuda_status(cudaMemsetAsync(h->nact_d, 0, sizeof(int), h->st), "memset"));
       PROF(PC_SMALL, 0, 1,
            cuda_status(launch_krylov_givens(d, k, h->Hh, h->cs, h->gv, h->bnorm, h->active, h->steps, h->est, rtol,

@@ -28,17 +28,20 @@ def setup():
     return omm, wl, sp, wl.potential_values()
 
 
-def test_full_size_pole_solve_sampled_columns(setup):
+@pytest.mark.parametrize("gm", [3, 15])
+def test_full_size_pole_solve_sampled_columns(setup, gm):
+    """gm = 15 runs a whole restart cycle: every basis size from 1 to 15 vectors through the
+    CGS2 kernels at the full grid size."""
     omm, wl, sp, V = setup
     z, w = omm.poles_fermi(sp["lam1"], sp["lamN"], sp["lamN1"], wl.P)
-    prm = omm.default_params(precision=omm.OMM_MIXED, gmres_m=3, gmres_cycles=1, gmres_fixed=1)
+    prm = omm.default_params(precision=omm.OMM_MIXED, gmres_m=gm, gmres_cycles=1, gmres_fixed=1)
     s = omm.Solver(2, wl.m, wl.L, V, wl.N, shift=sp["sigma"], params=prm)
     s.set_poles(z, w)
     R = wl.initial_block(np.complex64)
     Y, st = s.pole_solve(torch.from_numpy(R).to("cuda"))
     Y = Y.cpu().numpy().astype(np.complex128)
     zo, wo = opoles.poles_conformal(sp["lam1"], sp["lamN"], sp["lamN1"], wl.P)
-    pc = PolePreconditioner(wl.shape, wl.L, V, sp["sigma"], zo, wo, mode="gmres", inner="spp", gmres_m=3,
+    pc = PolePreconditioner(wl.shape, wl.L, V, sp["sigma"], zo, wo, mode="gmres", inner="spp", gmres_m=gm,
                             cycles=1, fixed=True)
     for c in (0, 77):
         ref = pc(R[c:c + 1].astype(np.complex128))[0]

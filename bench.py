@@ -498,10 +498,10 @@ def run_ours(a):
 # workload's systems), keyed by (workload, N, class); absent until captured for the class's
 # current kernels.
 TRAFFIC_PER_CALL = {
-    # profiles/traffic_trsv_smooth2d-128_N64.md: 197.7 MB read per call at N = 64 (S = 512),
-    # the vector part scaled to S = 1024, the factor part (71.0 MB) as measured; writes stay
+    # profiles/traffic_trsv_smooth2d-128_N64.md: 192.8 MB read per call at N = 64 (S = 512),
+    # the vector part scaled to S = 1024, the factor part (66.1 MB) as measured; writes stay
     # in L2 and are not attributed to these kernels
-    ("smooth2d-128", 128, "trsv_levels"): 324.0e6,
+    ("smooth2d-128", 128, "trsv_levels"): 319.5e6,
 }
 
 

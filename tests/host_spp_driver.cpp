@@ -11,6 +11,11 @@
 //         the same order --, L_SS^-1 and U_SS^-1 by columns, the W products) on the host and
 //         print "mapsdiff" with the largest differences from the host factor, relative to
 //         the largest entry
+//         or "tri" -- print "tri host <nonzeros> <entries>" (and "tri maps ..." for the
+//         replayed device factorisation): the entries of the zero triangles (above the
+//         diagonal of L_SS^-1 in W_f, below the diagonal of U_SS^-1 in W_b) of every node
+//         whose solves run through W, and how many of them are not exactly zero; the
+//         supernode products skip those triangles
 // stdin:  dim m L shift z_re z_im, then n values of V, then n pairs (re, im) of b
 // stdout: "dense" then n pairs of x (every node through W), and for 2D "banded" then n
 //         pairs of x (leaves through the banded data)
@@ -215,6 +220,31 @@ static bool factor_with_maps(const SppStructure& st, const SppFactorMaps& mp, co
   return true;
 }
 
+// Entries of the zero triangles of the W blocks of every node solved through W (all
+// nodes but the banded 2D leaves), and how many are not exactly zero.
+static void tri_count(const SppStructure& st, const std::vector<cd>& factor, long* nonzero, long* entries) {
+  *nonzero = 0;
+  *entries = 0;
+  for (size_t id = 0; id < st.nodes.size(); ++id) {
+    if (std::binary_search(st.leaf_nodes.begin(), st.leaf_nodes.end(), (int)id)) continue;
+    const SppNode& nd = st.nodes[id];
+    const int ns = nd.ns, kb = nd.ns + nd.nb;
+    const cd* wf = &factor[nd.wf];
+    const cd* wb = &factor[nd.wb];
+    for (int r = 0; r < ns; ++r)
+      for (int k = 0; k < ns; ++k) {
+        if (k > r) {
+          ++*entries;
+          if (wf[(size_t)r * ns + k] != cd(0, 0)) ++*nonzero;
+        }
+        if (k < r) {
+          ++*entries;
+          if (wb[(size_t)r * kb + k] != cd(0, 0)) ++*nonzero;
+        }
+      }
+  }
+}
+
 static double max_rel_diff(const std::vector<cd>& a, const std::vector<cd>& b) {
   double mx = 0, d = 0;
   for (size_t i = 0; i < a.size(); ++i) {
@@ -243,6 +273,21 @@ int main(int argc, char** argv) {
   SppPole pp;
   std::vector<cd> gh;
   spp_setup_pole(st, 2.0 * M_PI * M_PI / (L * L), V.data(), shift, cd(zr, zi), 1e-12, pp, gh, threads);
+  if (argc > 2 && std::string(argv[2]) == "tri") {
+    long nz = 0, ne = 0;
+    tri_count(st, pp.factor, &nz, &ne);
+    printf("tri host %ld %ld\n", nz, ne);
+    const SppFactorMaps mp = spp_factor_maps(st);
+    if (mp.ok) {
+      SppStencil sten;
+      std::vector<cd> gh2, fac, lv;
+      spp_pole_stencil(st, 2.0 * M_PI * M_PI / (L * L), V.data(), shift, cd(zr, zi), sten, gh2);
+      factor_with_maps(st, mp, sten, V, 1e-12, fac, lv);
+      tri_count(st, fac, &nz, &ne);
+      printf("tri maps %ld %ld\n", nz, ne);
+    }
+    return 0;
+  }
   if (argc > 2 && std::string(argv[2]) == "maps") {
     const SppFactorMaps mp = spp_factor_maps(st);
     if (!mp.ok) {

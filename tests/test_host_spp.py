@@ -107,3 +107,25 @@ def test_device_factor_maps_reproduce_the_host_factor(driver, dim, m, L):
     dfac, dleaf = float(line[1]), float(line[2])
     assert dfac < 1e-11, dfac
     assert dleaf < 1e-11, dleaf
+
+
+@pytest.mark.parametrize("dim,m,L", [(2, 32, 10.0), (3, 8, 20.0), (3, 12, 20.0)])
+def test_triangular_inverses_are_exactly_triangular(driver, dim, m, L):
+    """The supernode products run each row block only over the k range where L_SS^-1 (the
+    top block of W_f) and U_SS^-1 (the left block of W_b) can be nonzero: every entry above
+    the diagonal of L_SS^-1 and below the diagonal of U_SS^-1 is exactly zero, in the host
+    factor and in the device factorisation's schedule replayed on the host.  (On the device,
+    fa_tinv stores zeros in the 32 x 32 tiles across the diagonal, and its diagonal-tile
+    substitutions sum products with zero there; test_gpu_factor compares the resulting
+    preconditioner with the host factor's.)"""
+    shape = (m,) * dim
+    V = wells_2d(m, L, seed=9) if dim == 2 else lattice_wells_3d(m, L, cells=2)
+    shift = ham.default_shift(shape, L, V)
+    z = complex(-0.4 * shift, 0.6)
+    n = m ** dim
+    out = run_driver(driver, dim, m, L, V, shift, z, np.ones(n, dtype=complex), raw=True, extra=("tri",))
+    rows = {ln.split()[1]: (int(ln.split()[2]), int(ln.split()[3])) for ln in out.splitlines() if ln.startswith("tri")}
+    assert set(rows) == {"host", "maps"}
+    for who, (nonzero, entries) in rows.items():
+        assert entries > 0, who
+        assert nonzero == 0, (who, nonzero, entries)

@@ -135,6 +135,48 @@ struct Builder {
   }
 };
 
+// out[x] = sum_k in[k * istride] W^{k x} for x < len, W = e^{+2 pi i / len}, by decimation in
+// time over the smallest prime factor r of len: r transforms of length len / r over the
+// residues k = s (mod r), then X[k + q t] = sum_s W^{s (k + q t)} Y_s[k] (q = len / r).  A
+// prime length is one direct sum.  w[j] = e^{+2 pi i j / M} with M = len * wstep.
+void dft_plus(const cd* in, int istride, cd* out, int len, const cd* w, int wstep, int M) {
+  if (len == 1) {
+    out[0] = in[0];
+    return;
+  }
+  int r = len;
+  for (int f = 2; f * f <= len; ++f)
+    if (len % f == 0) {
+      r = f;
+      break;
+    }
+  const int q = len / r;
+  for (int s = 0; s < r; ++s) dft_plus(in + (size_t)s * istride, istride * r, out + (size_t)s * q, q, w, wstep * r, M);
+  cd ys[8];
+  std::vector<cd> yv;
+  cd* y = ys;
+  if (r > 8) {
+    yv.resize(r);
+    y = yv.data();
+  }
+  for (int k = 0; k < q; ++k) {
+    for (int s = 0; s < r; ++s) y[s] = out[(size_t)s * q + k];
+    for (int t = 0; t < r; ++t) {
+      const int x = k + q * t;
+      double re = 0.0, im = 0.0;
+      int e = 0;   // s x mod len
+      for (int s = 0; s < r; ++s) {
+        const cd a = y[s], b = w[(size_t)e * wstep];
+        re += a.real() * b.real() - a.imag() * b.imag();
+        im += a.real() * b.imag() + a.imag() * b.real();
+        e += x;
+        if (e >= len) e -= len;
+      }
+      out[x] = cd(re, im);
+    }
+  }
+}
+
 // separable inverse DFT with the 1/n already folded into the input: out[x] = sum_k in[k] e^{+2 pi i k.x/m}
 void idft_separable(int dim, int m, std::vector<cd>& a) {
   std::vector<cd> tw(m);
@@ -143,18 +185,13 @@ void idft_separable(int dim, int m, std::vector<cd>& a) {
   const int n = (dim == 3) ? m * m * m : m * m;
   for (int axis = 0; axis < dim; ++axis) {
     const int stride = axis == 0 ? 1 : (axis == 1 ? m : m * m);
-    for (int base = 0; base < n; ++base) {
-      // base must have coordinate 0 along axis
-      const int coord = (base / stride) % m;
-      if (coord != 0) continue;
-      for (int t = 0; t < m; ++t) line[t] = a[base + t * stride];
-      for (int x = 0; x < m; ++x) {
-        cd s(0.0, 0.0);
-        for (int k = 0; k < m; ++k) s += line[k] * tw[(k * x) % m];
-        res[x] = s;
+    for (int outer = 0; outer < n / (m * stride); ++outer)
+      for (int inner = 0; inner < stride; ++inner) {
+        const size_t base = (size_t)outer * m * stride + inner;
+        for (int t = 0; t < m; ++t) line[t] = a[base + (size_t)t * stride];
+        dft_plus(line.data(), 1, res.data(), m, tw.data(), 1, m);
+        for (int t = 0; t < m; ++t) a[base + (size_t)t * stride] = res[t];
       }
-      for (int t = 0; t < m; ++t) a[base + t * stride] = res[t];
-    }
   }
 }
 
@@ -468,7 +505,7 @@ SppStructure spp_build_structure(int dim, int m, int r) {
 void green_symbol(int dim, int m, double kin, double lmean, double shift, cd z, std::vector<cd>& ghat) {
   const int n = (dim == 3) ? m * m * m : m * m;
   ghat.resize(n);
-  auto sk = [m](int i) { return i < m / 2 ? i : i - m; };
+  auto sk = [m](int i) { return i < (m + 1) / 2 ? i : i - m; };   // DFT order; the same as m / 2 for even m
   for (int i = 0; i < n; ++i) {
     const int ix = i % m, iy = (i / m) % m, iz = (dim == 3) ? i / (m * m) : 0;
     const double k2 = (double)sk(ix) * sk(ix) + (double)sk(iy) * sk(iy) + (dim == 3 ? (double)sk(iz) * sk(iz) : 0.0);

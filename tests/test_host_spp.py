@@ -59,7 +59,8 @@ def phase_free_err(x, ref):
     return float(np.linalg.norm(c * x - ref) / np.linalg.norm(ref)), abs(c)
 
 
-@pytest.mark.parametrize("dim,m,L", [(2, 16, 10.0), (2, 32, 10.0), (3, 8, 20.0), (3, 12, 20.0)])
+@pytest.mark.parametrize("dim,m,L", [(2, 16, 10.0), (2, 32, 10.0), (2, 27, 10.0), (2, 48, 10.0), (3, 8, 20.0),
+                                     (3, 12, 20.0)])
 def test_host_factor_solves_the_oracle_P(driver, dim, m, L):
     shape = (m,) * dim
     V = wells_2d(m, L, seed=4) if dim == 2 else lattice_wells_3d(m, L, cells=2)

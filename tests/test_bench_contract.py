@@ -167,3 +167,24 @@ def test_serve_line_counts_failed_requests(bench, monkeypatch):
     monkeypatch.setattr(lib, "Solver", flaky.Solver)
     rec = run(b, b.run_many, ["--mode", "serve", "--requests", "10", "--rate", "100"], monkeypatch)
     assert rec["requests"] == 10 and rec["failed"] == 2 and "CUDA runtime" in rec["first_error"]
+
+
+def test_small_workload_times_one_whole_oracle_solve(bench, monkeypatch):
+    """wells2d-32 finishes a whole oracle solve in seconds: the CPU baseline times one (the
+    oracle's solve is stubbed here; its arithmetic has its own tests), with the poles'
+    factorisations built before the timed call."""
+    b, _ = bench
+    from oracle import solve as osolve
+    sp = json.load(open(os.path.join(ROOT, "workloads", "spectra.json")))["wells2d-32"]
+    calls = []
+
+    def fake_solve(shape, L, V, shift, X0, z, w, maxit=20, tol=1e-13, refilter=0, precond=None, **kw):
+        calls.append(dict(maxit=maxit, tol=tol, refilter=refilter, precond=precond))
+        return X0, dict(history=[[None] * 14], E=sp["E_ref"], precond=precond)
+
+    monkeypatch.setattr(osolve, "solve", fake_solve)
+    rec = run(b, b.run_ours, ["--workload", "wells2d-32", "--no-fp64-check", "--steps", "1"], monkeypatch)
+    cb = rec["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["unit"] == "solves/s" and cb["value"] > 0
+    assert cb["sample"].startswith("one whole oracle solve") and "13 CG iterations" in cb["sample"]
+    assert len(calls) == 1 and calls[0]["precond"] is not None and calls[0]["maxit"] == 40

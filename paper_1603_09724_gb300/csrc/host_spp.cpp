@@ -13,7 +13,6 @@
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
-#include <set>
 #include <thread>
 
 #include "spp.h"
@@ -119,20 +118,26 @@ struct Builder {
       if (b.per[d]) { lo[d] = 0; ext[d] = m; }
       else { lo[d] = b.lo[d] - r; ext[d] = std::min(m, b.ext[d] + 2 * r); }
     }
-    std::set<int> inside;
+    // membership by stamps in one array over the grid: points of b get stamp_in, points
+    // already emitted stamp_seen (fresh values per call, so earlier calls' marks never match)
+    if (mark.empty()) mark.assign((size_t)st->n, 0);
+    const int stamp_in = ++stamp, stamp_seen = ++stamp;
     {
       std::vector<int> pts;
       points(b, pts);
-      inside.insert(pts.begin(), pts.end());
+      for (int p : pts) mark[p] = stamp_in;
     }
-    std::set<int> seen;
     for (int tz = 0; tz < ext[2]; ++tz)
       for (int ty = 0; ty < ext[1]; ++ty)
         for (int tx = 0; tx < ext[0]; ++tx) {
           const int p = flat(wrap(lo[0] + tx, m), wrap(lo[1] + ty, m), dim == 3 ? wrap(lo[2] + tz, m) : 0);
-          if (!inside.count(p) && seen.insert(p).second) out.push_back(p);
+          if (mark[p] == stamp_in || mark[p] == stamp_seen) continue;
+          mark[p] = stamp_seen;
+          out.push_back(p);
         }
   }
+  mutable std::vector<int> mark;   // halo(): per grid point, the stamp of its last visit
+  mutable int stamp = 0;
 };
 
 // out[x] = sum_k in[k * istride] W^{k x} for x < len, W = e^{+2 pi i / len}, by decimation in
@@ -445,16 +450,18 @@ SppStructure spp_build_structure(int dim, int m, int r) {
       if (bd.node_children_a[i] >= 0) ischild[i] = 1;
       if (bd.node_children_b[i] >= 0) ischild[i] = 1;
     }
+    // periodic Chebyshev distance between grid points, from their coordinates
+    std::vector<int> crd((size_t)st.n * 2);
+    for (int p = 0; p < st.n; ++p) {
+      crd[2 * (size_t)p] = p % m;
+      crd[2 * (size_t)p + 1] = p / m;
+    }
     auto cheb = [&](int p, int q) {
-      int d = 0;
-      int pc[3] = {p % m, (p / m) % m, dim == 3 ? p / (m * m) : 0};
-      int qc[3] = {q % m, (q / m) % m, dim == 3 ? q / (m * m) : 0};
-      for (int a = 0; a < dim; ++a) {
-        int t = std::abs(pc[a] - qc[a]);
-        t = std::min(t, m - t);
-        d = std::max(d, t);
-      }
-      return d;
+      int tx = std::abs(crd[2 * (size_t)p] - crd[2 * (size_t)q]);
+      int ty = std::abs(crd[2 * (size_t)p + 1] - crd[2 * (size_t)q + 1]);
+      tx = std::min(tx, m - tx);
+      ty = std::min(ty, m - ty);
+      return std::max(tx, ty);
     };
     long long vo = 0;
     for (int i = 0; i < nn; ++i) {

@@ -25,6 +25,9 @@ def test_reference_arm_prints_one_contract_line():
     assert rec["e2e"] == {"value": rec["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
     assert rec["config"]["workload"].startswith("wells2d-32")
+    # the config states the refilter rounds the sample is scaled to (bench.py's default: 1)
+    assert rec["config"]["refilter"] == 1 and "refilter_rtol" not in rec["config"]
+    assert "rtol 1e-05" in rec["config"]["gmres"]
 
 
 def test_roofline_record_bounds_and_arithmetic():
